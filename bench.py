@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Throughput of the device-wide sum on GB300.
+
+One step = one call of the library's reduction over the whole headline
+workload: n = 2^28 binary32 values drawn U[-1, 1] (seed 0), 1 GiB, resident in
+HBM before timing starts.  The input is larger than L2 (129 MB), so no flush is
+needed between steps.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun), every rank reduces its own copy of the workload on its
+own GPU (independent replicas: the path has no exchange step on one box);
+value = bytes reduced by all ranks / max-over-ranks time.
+"""
+import argparse
+import ctypes
+import glob
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Reduce GB/s & %HBM peak at 2^28 FP32; µs at 2^14; batched vs plain speedup"
+N_HEADLINE = 1 << 28
+N_LATENCY = 1 << 14
+WORKLOAD = "device-wide sum, n=2^28 FP32 U[-1,1] seed 0 (1 GiB)"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------- traffic record
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2004_05371_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    or None when the summary was taken on a different kernel source."""
+    src = kernel_source_hash()
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(p) as f:
+            text = f.read()
+        m = re.search(r"traffic_record:\s*kernel=(\S+)\s+source=(\S+)\s+bytes_per_launch=(\d+)", text)
+        if m and m.group(1) == kernel_tag and m.group(2) == src:
+            return int(m.group(3))
+    return None
+
+
+# -------------------------------------------------------------- CPU baseline
+def cpu_baseline(seconds=10.0):
+    """The oracle (sequential FP64 loop, one host thread) on a bounded sample."""
+    import numpy as np
+    import oracle
+    import workloads
+    n = 1 << 25
+    x = workloads.uniform_f32(n, seed=0)
+    oracle.sum_f32(x[:1024])
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sum_f32(x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    gbs = reps * n * 4 / el / 1e9
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d passes of the sequential FP64 loop over the first 2^25 elements (128 MiB) of the "
+                      "same U[-1,1] seed-0 workload, %.1f s" % (reps, el),
+            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = []
+    import oracle
+    import workloads
+    n = 1 << 25
+    x = workloads.uniform_f32(n, seed=0)
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.sum_f32(x)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            per_step.append(dt)
+    el = sum(per_step)
+    gbs = args.steps * n * 4 / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "first 2^25 elements per step (the oracle is a "
+                                                        "sequential CPU loop)", "l2": "input > L2"},
+            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "first 2^25 elements (128 MiB) of the workload per step"},
+            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", type=lambda s: int(s, 0), default=None,
+                    help="explicit variant bits (default: the library's AUTO choice)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--n", type=int, default=N_HEADLINE, help="elements (profiling runs use a smaller case)")
+    ap.add_argument("--skip-extras", action="store_true", help="headline loop only (profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2004_05371_gb300 as sr
+    import workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sr.load()
+
+    variant = sr.AUTO if args.variant is None else args.variant
+    cfg = sr.make_config(variant)
+    N = args.n
+    resolved = sr.plan(N, sr.F32, cfg)
+    stage = resolved.variant & sr.STAGE_MASK
+    launches_per_step = 2 if stage == sr.TWO_KERNEL else 1
+
+    x_host = workloads.uniform_f32(N, seed=0)
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def step():
+        sr.check(sr.reduce_sum_ptr(x.data_ptr(), N, sr.F32, out.data_ptr(), cfg, sh))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    # per-launch events on the launching stream (the kernel's own duration)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if pg:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    assert sr.stream_status(sh) == sr.OK
+
+    bytes_step = N * 4
+    value = ws * args.steps * bytes_step / (elapsed_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    kernel_ms = statistics.mean(per_launch_ms)
+    achieved = bytes_step / (kernel_ms * 1e-3) / 1e9
+    kernel_tag = "reduce_%s" % ("bulk" if resolved.variant & sr.F_BULK else "ldg")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kernel_tag),
+                "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_kind
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": kernel_tag, "algorithmic_bytes_per_launch": bytes_step,
+                "per_launch_us": round(kernel_ms * 1e3, 2)}
+
+    # ---- secondary: latency at 2^14 (device time per call inside a graph of calls)
+    secondary, e2e = None, None
+    if not args.skip_extras:
+        secondary = {}
+        try:
+            secondary["latency_2p14_us"] = latency_small(sr, torch, dev, stream)
+        except Exception as e:  # reported, never hides the headline
+            secondary["latency_2p14_error"] = str(e)[:200]
+        # ---- end to end: input in pinned host memory, copies inside the timed region
+        try:
+            e2e = end_to_end(sr, torch, dev, stream, x_host, args)
+        except Exception as e:
+            e2e = {"error": str(e)[:200]}
+        if pg and e2e and "value" in e2e:
+            t = torch.tensor([e2e["value"]], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MIN)
+            e2e["value"] = float(t.item()) * ws
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.skip_extras:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD if N == N_HEADLINE else "device-wide sum, n=%d FP32 U[-1,1] seed 0" % N, "n": N, "variant": "0x%x" % resolved.variant,
+                           "stage": sr.STAGE_NAMES.get(stage), "grid": resolved.grid,
+                           "block": resolved.block_threads, "vec_bytes": resolved.vec_bytes,
+                           "unroll": resolved.unroll, "tile_bytes": resolved.tile_bytes,
+                           "stages": resolved.stages, "l2": "input (1 GiB) larger than L2: no flush",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "pct_hbm_peak": round(value / ws / peak, 4),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk, "secondary": secondary}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def latency_small(sr, torch, dev, stream):
+    """Device time per call at n=2^14 (AUTO choice), averaged over a CUDA graph
+    of 200 back-to-back calls, plus the host round trip of a single call."""
+    import workloads
+    x = torch.from_numpy(workloads.uniform_f32(N_LATENCY, seed=0)).to(dev)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    cfg = sr.make_config(sr.AUTO)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg, s.cuda_stream))
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    calls = 200
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(calls):
+            sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg,
+                                       torch.cuda.current_stream().cuda_stream))
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    graph_us = a.elapsed_time(b) * 1e3 / (reps * calls)
+    rt = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg, stream.cuda_stream))
+        stream.synchronize()
+        rt.append((time.perf_counter() - t0) * 1e6)
+    return {"graph_us_per_call": round(graph_us, 3), "host_roundtrip_us_median": round(statistics.median(rt), 2),
+            "variant": "0x%x" % sr.plan(N_LATENCY, sr.F32, cfg).variant}
+
+
+def end_to_end(sr, torch, dev, stream, x_host, args):
+    """The same metric with the input in pinned HOST memory: every step copies
+    the 1 GiB input host->device, reduces it and reads the scalar back."""
+    import numpy as np
+    n = x_host.size
+    pinned = torch.from_numpy(x_host).pin_memory()
+    res = torch.empty((), dtype=torch.float32).pin_memory()
+    xd = torch.empty(n, dtype=torch.float32, device=dev)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    cfg = sr.make_config(sr.AUTO)
+
+    def step():
+        xd.copy_(pinned, non_blocking=True)
+        sr.check(sr.reduce_sum_ptr(xd.data_ptr(), n, sr.F32, out.data_ptr(), cfg, stream.cuda_stream))
+        res.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    k = max(3, min(args.steps, 10))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(k):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / k
+    return {"value": round(n * 4 / (ms * 1e-3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": n * 4,
+            "d2h_bytes_per_step": 4, "ms_per_step": round(ms, 3),
+            "path": "pinned host -> device copy (cudaMemcpyAsync) + sr_reduce_sum_ex + 4-byte read-back"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

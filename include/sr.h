@@ -1,0 +1,162 @@
+/*
+ * sr.h — C ABI of the GB300 (sm_103a) device-wide sum reduction library.
+ *
+ * The operation is the case study of Zhang, Wahib, Zhang and Matsuoka, "A
+ * Study of Single and Multi-device Synchronization Methods in Nvidia GPUs"
+ * (arXiv 2004.05371), Section VII: summing the elements of an array,
+ * S = sum_{i<n} x_i, computed by stages joined by a barrier at each level of
+ * the GPU hierarchy (Section III-A): per-thread accumulation (Fig.
+ * "Basic function of device wide reduction", summing()), a warp shuffle tree
+ * (Section VII-D, Table V), a shared-memory block tree joined by the block
+ * barrier (block_reduce(), same figure), a thread-block-cluster merge through
+ * distributed shared memory (sm_90+; no counterpart in the paper), and a grid
+ * stage in one of the forms the paper compares (Section VII-E): the implicit
+ * kernel-boundary barrier of a two-kernel reduction (Fig. "Code example of
+ * reduction with implicit device synchronization"), a cooperative persistent
+ * kernel with grid.sync() (Fig. "Code example of reduction with explicit
+ * device synchronization"), plus two non-barrier finishes (atomics, and a
+ * __threadfence last-block-done ticket).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named x, offsets, out are DEVICE pointers owned by the caller;
+ *    the library never frees or retains them past the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Reductions are
+ *    stream-ordered and asynchronous: `out` is valid once the stream has
+ *    reached the end of the call's work (e.g. after cudaStreamSynchronize).
+ *  - The library owns a small workspace per (device, stream) pair (partials,
+ *    ticket counters, an error word).  It is allocated with cudaMalloc on the
+ *    first call that uses that pair, so the first call on a stream must not be
+ *    made while the stream is being captured into a CUDA graph.  Calls on
+ *    different streams never share a workspace.
+ *  - Arguments are validated before anything is launched; an invalid call
+ *    returns an error status and launches nothing.
+ *  - Return value: an sr_status.  SR_ERR_CUDA means a CUDA runtime call failed;
+ *    sr_last_cuda_error() returns its cudaError_t for the calling thread.
+ *  - No entry point falls back to the CPU.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sr_stream_t; /* identical to cudaStream_t */
+
+/* ------------------------------------------------------------ enums */
+
+typedef enum {
+    SR_F32 = 0,      /* binary32 in, binary32 out (binary64 with SR_F_FP64_COMBINE) */
+    SR_I32 = 1,      /* int32 in, int64 out, exact (bit-exact with the definition) */
+    SR_BF16 = 2,     /* bfloat16 in, binary32 accumulation and out */
+    SR_FP8E4M3 = 3   /* FP8 E4M3 (OCP E4M3FN) codes in, binary32 accumulation;
+                        the result is multiplied once by sr_config.scale */
+} sr_dtype;
+
+/* Grid stage: bits 0-3 of a variant. */
+typedef enum {
+    SR_AUTO = 0,           /* library chooses stage, cluster and launch shape */
+    SR_TWO_KERNEL = 1,     /* implicit barrier: kernel 1 writes one partial per unit,
+                              kernel 2 (one block) reduces them (Section III-B-2, VII-E) */
+    SR_ATOMIC = 2,         /* each unit atomically adds its partial into out (out is
+                              zeroed first); FP order is not deterministic */
+    SR_LAST_BLOCK = 3,     /* partial store, __threadfence, ticket; the last unit to
+                              arrive reduces all partials (one kernel, no spin) */
+    SR_GRID_SYNC = 4,      /* cooperative persistent kernel: partials, grid.sync(),
+                              block 0 reduces (Section III-A-3, VII-E) */
+    SR_SINGLE_CLUSTER = 5  /* one cluster (or one CTA) covers the whole array: no grid
+                              stage at all; for small n */
+} sr_stage;
+
+#define SR_STAGE_MASK 0xF
+/* Cluster size of a unit, bits 4-6: 0 -> 1 CTA per unit (no cluster stage),
+ * k in 1..4 -> 2^k CTAs per cluster, merged through distributed shared
+ * memory before the grid stage.  16 uses the non-portable cluster size. */
+#define SR_CLUSTER_SHIFT 4
+#define SR_CLUSTER_MASK 0x70
+#define SR_CLUSTER(log2c) (((log2c) & 7) << SR_CLUSTER_SHIFT)
+/* Flags. */
+#define SR_F_KAHAN 0x100        /* two-sum compensated accumulation, (sum, correction)
+                                   pairs carried through every tree level */
+#define SR_F_FP64_COMBINE 0x200 /* unit partials converted to binary64 and combined in
+                                   binary64; `out` is then a double */
+#define SR_F_BULK 0x400         /* load path: TMA bulk copies (cp.async.bulk) into a
+                                   shared-memory ring instead of 128/256-bit LDG */
+
+typedef enum {
+    SR_OK = 0,
+    SR_ERR_ARG = 1,         /* bad pointer, size, alignment or config value */
+    SR_ERR_DTYPE = 2,       /* unknown dtype, or dtype not allowed for this call */
+    SR_ERR_LAUNCH = 3,      /* launch shape impossible (e.g. a cooperative grid that
+                               cannot be co-resident); nothing was launched */
+    SR_ERR_CUDA = 4,        /* a CUDA runtime call failed: see sr_last_cuda_error() */
+    SR_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired (reported by
+                               sr_stream_status) */
+    SR_ERR_UNSUPPORTED = 6  /* valid but unsupported combination of options */
+} sr_status;
+
+/* Barrier levels of sr_barrier_bench (Section V, Fig. "Hierarchy of
+ * synchronizations in CUDA"; the cluster level is sm_90+ only). */
+typedef enum {
+    SR_LEVEL_WARP = 0,       /* tile (warp) sync, bar.warp.sync */
+    SR_LEVEL_COALESCED = 1,  /* coalesced-group sync over the active lanes */
+    SR_LEVEL_BLOCK = 2,      /* __syncthreads */
+    SR_LEVEL_CLUSTER = 3,    /* barrier.cluster arrive/wait */
+    SR_LEVEL_GRID = 4,       /* cooperative grid.sync() */
+    SR_LEVEL_KERNEL = 5,     /* implicit kernel-boundary barrier: launch overhead by
+                                the kernel-fusion method (Eq. 6) */
+    SR_LEVEL_SHUFFLE = 6     /* dependent __shfl_xor_sync chain (Table II "Shuffle") */
+} sr_level;
+
+/* Launch configuration.  Zero in any field means "library default". */
+typedef struct {
+    int variant;        /* stage | SR_CLUSTER(k) | flags */
+    int block_threads;  /* threads per CTA (multiple of 32, <= 1024) */
+    int ctas_per_sm;    /* resident CTAs per SM the grid is sized for */
+    int grid;           /* explicit CTA count (overrides ctas_per_sm); rounded up to a
+                           multiple of the cluster size */
+    int vec_bytes;      /* LDG path: bytes per vector load, 16 or 32 */
+    int unroll;         /* LDG path: independent vector loads in flight per thread, 1..8 */
+    int tile_bytes;     /* BULK path: bytes per TMA copy / ring stage (multiple of 1024) */
+    int stages;         /* BULK path: ring depth, 2..8 */
+    float scale;        /* FP8: factor applied once to the final sum (0 -> 1) */
+    int reserved[3];
+} sr_config;
+
+/* --------------------------------------------------- single-array sum */
+
+/* S = sum_{i<n} x_i (Section VII).  x: device array of n elements of `dtype`,
+ * aligned to the element size.  out: device scalar — int64 for SR_I32, float
+ * otherwise, double when SR_F_FP64_COMBINE is set.  n == 0 writes 0.
+ * Errors: SR_ERR_ARG (n < 0, NULL x with n > 0, NULL out, misaligned x or out),
+ * SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
+int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant,
+                  sr_stream_t stream);
+
+/* Same with an explicit launch configuration (NULL cfg = defaults). */
+int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out,
+                     const sr_config* cfg, sr_stream_t stream);
+
+/* Synchronise `stream` and report (and clear) device-side error flags raised
+ * by this library's kernels on it since the last call: SR_ERR_TIMEOUT when a
+ * bounded wait expired, else SR_OK (or SR_ERR_CUDA). */
+int sr_stream_status(sr_stream_t stream);
+
+/* Resolve the launch shape the library would use for this call on the
+ * current device, without launching: fills *resolved (variant with the
+ * stage chosen, block_threads, grid, vec_bytes, unroll, tile_bytes, stages).
+ * Needs a device; returns the same errors sr_reduce_sum_ex would. */
+int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
+
+/* ------------------------------------------------------ host helpers */
+
+const char* sr_status_string(int status);
+int sr_last_cuda_error(void);
+const char* sr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR_H */

@@ -1,0 +1,170 @@
+"""Python binding of ``libsr.so`` (the C ABI declared in ``include/sr.h``).
+
+Argument marshalling only: every step of the reduction runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams; no torch kernel is
+used on the path.  If the library has not been built this module raises: there
+is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsr.so")
+
+# dtypes (sr_dtype)
+F32, I32, BF16, FP8E4M3 = 0, 1, 2, 3
+# grid stages (sr_stage)
+AUTO, TWO_KERNEL, ATOMIC, LAST_BLOCK, GRID_SYNC, SINGLE_CLUSTER = 0, 1, 2, 3, 4, 5
+STAGE_NAMES = {AUTO: "auto", TWO_KERNEL: "two_kernel", ATOMIC: "atomic", LAST_BLOCK: "last_block",
+               GRID_SYNC: "grid_sync", SINGLE_CLUSTER: "single_cluster"}
+STAGE_MASK = 0xF
+CLUSTER_SHIFT = 4
+CLUSTER_MASK = 0x70
+F_KAHAN = 0x100
+F_FP64_COMBINE = 0x200
+F_BULK = 0x400
+# status codes (sr_status)
+OK, ERR_ARG, ERR_DTYPE, ERR_LAUNCH, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+# barrier levels (sr_level)
+LEVEL_WARP, LEVEL_COALESCED, LEVEL_BLOCK, LEVEL_CLUSTER, LEVEL_GRID, LEVEL_KERNEL, LEVEL_SHUFFLE = range(7)
+
+
+def CLUSTER(log2c: int) -> int:
+    return (log2c & 7) << CLUSTER_SHIFT
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``sr_config``."""
+    _fields_ = [("variant", ctypes.c_int), ("block_threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("grid", ctypes.c_int), ("vec_bytes", ctypes.c_int), ("unroll", ctypes.c_int),
+                ("tile_bytes", ctypes.c_int), ("stages", ctypes.c_int), ("scale", ctypes.c_float),
+                ("reserved", ctypes.c_int * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class SRError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        if status == ERR_CUDA and _lib is not None:
+            msg += " (cudaError %d)" % _lib.sr_last_cuda_error()
+        super().__init__("%s%s" % (what + ": " if what else "", msg))
+
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsr.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.sr_reduce_sum.restype = i32
+    L.sr_reduce_sum.argtypes = [vp, i64, i32, vp, i32, vp]
+    L.sr_reduce_sum_ex.restype = i32
+    L.sr_reduce_sum_ex.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
+    L.sr_stream_status.restype = i32
+    L.sr_stream_status.argtypes = [vp]
+    L.sr_plan.restype = i32
+    L.sr_plan.argtypes = [i64, i32, ctypes.POINTER(Config), ctypes.POINTER(Config)]
+    L.sr_status_string.restype = ctypes.c_char_p
+    L.sr_status_string.argtypes = [i32]
+    L.sr_last_cuda_error.restype = i32
+    L.sr_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def lib():
+    return load()
+
+
+def status_string(status: int) -> str:
+    return lib().sr_status_string(int(status)).decode()
+
+
+def version() -> str:
+    return lib().sr_version().decode()
+
+
+def check(status: int, what: str = ""):
+    if status != OK:
+        raise SRError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dtype_code(t) -> int:
+    import torch
+    m = {torch.float32: F32, torch.int32: I32, torch.bfloat16: BF16, torch.uint8: FP8E4M3}
+    fp8 = getattr(torch, "float8_e4m3fn", None)
+    if fp8 is not None:
+        m[fp8] = FP8E4M3
+    if t.dtype not in m:
+        raise TypeError("unsupported dtype %s" % t.dtype)
+    return m[t.dtype]
+
+
+def out_dtype(dtype: int, variant: int):
+    import torch
+    if dtype == I32:
+        return torch.int64
+    return torch.float64 if variant & F_FP64_COMBINE else torch.float32
+
+
+def make_config(variant=AUTO, **kw) -> Config:
+    c = Config()
+    c.variant = int(variant)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def reduce_sum_ptr(x_ptr: int, n: int, dtype: int, out_ptr: int, config: Config = None, stream=None) -> int:
+    """Raw call of sr_reduce_sum_ex; returns the status (no raise)."""
+    cfg = ctypes.byref(config) if config is not None else None
+    return lib().sr_reduce_sum_ex(ctypes.c_void_p(x_ptr), int(n), int(dtype), ctypes.c_void_p(out_ptr), cfg,
+                                  ctypes.c_void_p(_stream(stream)))
+
+
+def reduce_sum(x, variant: int = AUTO, out=None, config: Config = None, stream=None, **cfg_fields):
+    """Sum of a contiguous 1-D CUDA tensor through sr_reduce_sum_ex.
+
+    Returns a 0-dim CUDA tensor (int64 for int32 input, float64 with
+    F_FP64_COMBINE, float32 otherwise).  uint8 input is read as FP8 E4M3 codes.
+    """
+    import torch
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor")
+    dt = dtype_code(x)
+    if config is None:
+        config = make_config(variant, **cfg_fields)
+    if out is None:
+        out = torch.empty((), dtype=out_dtype(dt, config.variant), device=x.device)
+    st = reduce_sum_ptr(x.data_ptr(), x.numel(), dt, out.data_ptr(), config, stream)
+    check(st, "sr_reduce_sum_ex")
+    return out
+
+
+def plan(n: int, dtype: int, config: Config = None) -> Config:
+    r = Config()
+    cfg = ctypes.byref(config) if config is not None else None
+    check(lib().sr_plan(int(n), int(dtype), cfg, ctypes.byref(r)), "sr_plan")
+    return r
+
+
+def stream_status(stream=None) -> int:
+    return lib().sr_stream_status(ctypes.c_void_p(_stream(stream)))

@@ -1,0 +1,245 @@
+// Device-side building blocks of the hierarchical sum (sm_103a).
+//
+// Thread stage  : vector loads + per-lane register accumulation
+//                 (summing(), Fig. "Basic function of device wide reduction").
+// Warp stage    : __shfl_down_sync tree, offsets 16..1 (Section VII-D; the
+//                 tile-shuffle form is the fastest correct warp reduction of
+//                 Table V).
+// Block stage   : warp leaders -> shared memory -> block barrier -> warp 0
+//                 (block_reduce(), same figure; the final stage over at most
+//                 32 values follows Table IV's "32 data points with a warp").
+// Cluster stage : partials written into the rank-0 CTA's shared memory
+//                 through distributed shared memory, then barrier.cluster.
+// TMA bulk path : cp.async.bulk global->shared copies completing on mbarriers,
+//                 every wait bounded by %globaltimer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cooperative_groups.h>
+
+namespace sr {
+namespace cg = cooperative_groups;
+
+constexpr int kDtF32 = 0, kDtI32 = 1, kDtBF16 = 2, kDtFP8 = 3;
+constexpr int kStageTwoKernel = 1, kStageAtomic = 2, kStageLastBlock = 3,
+              kStageGridSync = 4, kStageSingle = 5;
+
+
+// ------------------------------------------------------------------ loads
+// Read-only streaming loads: no L1 allocation (each byte is used once).
+__device__ __forceinline__ void ldg_vec(const void* p, uint32_t (&r)[4]) {
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "l"(p));
+}
+__device__ __forceinline__ void ldg_vec(const void* p, uint32_t (&r)[8]) {
+    asm("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]),
+          "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void lds_vec(uint32_t saddr, uint32_t (&r)[4]) {
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr));
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------ compensated pairs
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no contraction:
+// the explicit _rn intrinsics keep nvcc from fusing or reassociating).
+struct Pair { float s, c; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// ------------------------------------------------------ value operations
+// Accumulator / partial types: int64 (int32 input), float, Pair, double.
+template <class A> struct Op;
+template <> struct Op<long long> {
+    __device__ static long long zero() { return 0; }
+    __device__ static long long add(long long a, long long b) { return a + b; }
+    __device__ static long long shfl_down(long long v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+};
+template <> struct Op<float> {
+    __device__ static float zero() { return 0.f; }
+    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ static float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+};
+template <> struct Op<double> {
+    __device__ static double zero() { return 0.0; }
+    __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+};
+template <> struct Op<Pair> {
+    __device__ static Pair zero() { return Pair{0.f, 0.f}; }
+    // (s1,c1) + (s2,c2): TwoSum of the leading parts, corrections added.
+    __device__ static Pair add(Pair a, Pair b) {
+        float s, e;
+        two_sum(a.s, b.s, s, e);
+        return Pair{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+    }
+    __device__ static Pair shfl_down(Pair v, int o) {
+        return Pair{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+    }
+};
+
+template <class A> __device__ __forceinline__ A warp_reduce(A v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = Op<A>::add(v, Op<A>::shfl_down(v, o));
+    return v;
+}
+
+// Block tree: the result is valid in thread 0.  `scratch` holds 32 values.
+// Every thread of the block must call it (it contains block barriers).
+template <class A> __device__ __forceinline__ A block_reduce(A v, A* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    v = warp_reduce(v);
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    A r = Op<A>::zero();
+    if (warp == 0) {
+        r = lane < nwarps ? scratch[lane] : Op<A>::zero();
+        r = warp_reduce(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// --------------------------------------------------------------- per-dtype
+// Accumulator of the thread stage for each input type.
+template <int DT, bool COMP> struct Acc { using T = float; };
+template <> struct Acc<kDtI32, false> { using T = long long; };
+template <int DT> struct Acc<DT, true> { using T = Pair; };
+
+template <class A> __device__ __forceinline__ void acc_add_f(A& a, float v);
+template <> __device__ __forceinline__ void acc_add_f<float>(float& a, float v) { a = __fadd_rn(a, v); }
+template <> __device__ __forceinline__ void acc_add_f<Pair>(Pair& a, float v) {
+    float s, e;
+    two_sum(a.s, v, s, e);
+    a.s = s;
+    a.c = __fadd_rn(a.c, e);
+}
+
+// Add the elements packed in one 32-bit word into accumulator `a`.
+template <int DT, class A> __device__ __forceinline__ void acc_word(A& a, uint32_t w);
+template <> __device__ __forceinline__ void acc_word<kDtI32, long long>(long long& a, uint32_t w) {
+    a += (long long)(int)w;
+}
+template <> __device__ __forceinline__ void acc_word<kDtF32, float>(float& a, uint32_t w) { acc_add_f(a, __uint_as_float(w)); }
+template <> __device__ __forceinline__ void acc_word<kDtF32, Pair>(Pair& a, uint32_t w) { acc_add_f(a, __uint_as_float(w)); }
+// BF16: the two halves are the top 16 bits of binary32 words (exact).
+template <class A> __device__ __forceinline__ void acc_word_bf16(A& a, uint32_t w) {
+    acc_add_f(a, __uint_as_float(w << 16));
+    acc_add_f(a, __uint_as_float(w & 0xffff0000u));
+}
+template <> __device__ __forceinline__ void acc_word<kDtBF16, float>(float& a, uint32_t w) { acc_word_bf16(a, w); }
+template <> __device__ __forceinline__ void acc_word<kDtBF16, Pair>(Pair& a, uint32_t w) { acc_word_bf16(a, w); }
+// FP8 E4M3: hardware conversion to f16x2 (exact: f16 covers the E4M3 range
+// including its subnormals), then f16 -> f32 (exact).
+template <class A> __device__ __forceinline__ void acc_word_fp8(A& a, uint32_t w) {
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&lo));
+    float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&hi));
+    acc_add_f(a, f0.x);
+    acc_add_f(a, f0.y);
+    acc_add_f(a, f1.x);
+    acc_add_f(a, f1.y);
+}
+template <> __device__ __forceinline__ void acc_word<kDtFP8, float>(float& a, uint32_t w) { acc_word_fp8(a, w); }
+template <> __device__ __forceinline__ void acc_word<kDtFP8, Pair>(Pair& a, uint32_t w) { acc_word_fp8(a, w); }
+
+// One scalar element at index i of the input (head / tail of the vector body).
+template <int DT, class A> __device__ __forceinline__ void acc_elem(A& a, const unsigned char* x, int64_t i);
+template <> __device__ __forceinline__ void acc_elem<kDtI32, long long>(long long& a, const unsigned char* x, int64_t i) {
+    a += (long long)reinterpret_cast<const int*>(x)[i];
+}
+template <class A> __device__ __forceinline__ void acc_elem_f32(A& a, const unsigned char* x, int64_t i) {
+    acc_add_f(a, reinterpret_cast<const float*>(x)[i]);
+}
+template <class A> __device__ __forceinline__ void acc_elem_bf16(A& a, const unsigned char* x, int64_t i) {
+    uint32_t b = reinterpret_cast<const unsigned short*>(x)[i];
+    acc_add_f(a, __uint_as_float(b << 16));
+}
+template <class A> __device__ __forceinline__ void acc_elem_fp8(A& a, const unsigned char* x, int64_t i) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)x[i], __NV_E4M3);
+    acc_add_f(a, __half2float(*reinterpret_cast<__half*>(&h)));
+}
+template <> __device__ __forceinline__ void acc_elem<kDtF32, float>(float& a, const unsigned char* x, int64_t i) { acc_elem_f32(a, x, i); }
+template <> __device__ __forceinline__ void acc_elem<kDtF32, Pair>(Pair& a, const unsigned char* x, int64_t i) { acc_elem_f32(a, x, i); }
+template <> __device__ __forceinline__ void acc_elem<kDtBF16, float>(float& a, const unsigned char* x, int64_t i) { acc_elem_bf16(a, x, i); }
+template <> __device__ __forceinline__ void acc_elem<kDtBF16, Pair>(Pair& a, const unsigned char* x, int64_t i) { acc_elem_bf16(a, x, i); }
+template <> __device__ __forceinline__ void acc_elem<kDtFP8, float>(float& a, const unsigned char* x, int64_t i) { acc_elem_fp8(a, x, i); }
+template <> __device__ __forceinline__ void acc_elem<kDtFP8, Pair>(Pair& a, const unsigned char* x, int64_t i) { acc_elem_fp8(a, x, i); }
+
+// ------------------------------------------------------------ partials
+// A unit partial stored in the workspace: 16 bytes per slot.
+//   int32 input          -> int64
+//   float, no FP64 flag  -> float   (Pair when compensated)
+//   FP64 combine         -> double  (s + c converted exactly term by term)
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(Pair v) { return (double)v.s + (double)v.c; }
+__device__ __forceinline__ double to_double(long long v) { return (double)v; }
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(Pair v) { return __fadd_rn(v.s, v.c); }
+
+// ----------------------------------------------------------- mbarrier/TMA
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete.  Returns
+// false when `limit_ns` of %globaltimer time passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+// 1-D bulk copy global -> this CTA's shared memory; completes `bytes`
+// transaction bytes on `bar`.  dst, src 16-byte aligned; bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+}  // namespace sr

@@ -1,0 +1,77 @@
+// Host-side declarations shared by the C-ABI layer and the kernel
+// translation units.  Not part of the public interface (see include/sr.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sr.h"
+
+namespace sr {
+
+// Workspace owned by the library, one per (device, stream) pair.
+//   tickets[32]  : self-resetting arrival counters (last-block-done)
+//   err          : device-side error word (bounded waits that expired, ...)
+//   partials     : kMaxUnits slots of 16 bytes (one unit partial each)
+//   seg          : segmented-reduction carries
+constexpr int kMaxUnits = 65536;
+constexpr size_t kSlotBytes = 16;
+constexpr size_t kSegBytes = 4u << 20;
+constexpr size_t kHeaderBytes = 256;
+
+struct Workspace {
+    unsigned char* base = nullptr;
+    unsigned int* tickets = nullptr;
+    int* err = nullptr;
+    unsigned char* partials = nullptr;
+    unsigned char* seg = nullptr;
+};
+
+struct DeviceInfo {
+    int dev = 0;
+    int sms = 0;
+    int max_threads_per_sm = 0;
+    int max_blocks_per_sm = 0;
+    int smem_per_block_optin = 0;
+    int smem_per_sm = 0;
+    int l2_bytes = 0;
+    int cc_major = 0, cc_minor = 0;
+    int clock_khz = 0;
+};
+
+// A fully resolved single-array launch.
+struct Plan {
+    int dtype = 0, elem = 4;
+    int stage = 0, log2c = 0, cluster = 1;
+    bool comp = false, fp64 = false, bulk = false;
+    int block = 0, grid = 0, units = 0;
+    int vec = 16, unroll = 4;
+    int tile = 0, stages = 0;
+    size_t smem = 0;
+    float scale = 1.f;
+    // geometry of the input (filled by plan_geometry)
+    int64_t n = 0, head = 0, nvec = 0, tail_begin = 0, ntail = 0;
+    int64_t body_bytes = 0, ntiles = 0;
+};
+
+// C-ABI layer services
+int status_from_cuda(cudaError_t e);           // records the error, returns SR_ERR_CUDA
+const DeviceInfo* current_device(int* status);  // cached per device
+int get_workspace(cudaStream_t s, Workspace* ws);
+uint64_t spin_limit_ns();
+
+// Cached per-function launch facts (one query per function and shape).
+int prepare_function(const void* fn, size_t dyn_smem, bool nonportable_cluster);
+int blocks_per_sm(const DeviceInfo& d, const void* fn, int block, size_t dyn_smem, int* out);
+int active_clusters(const DeviceInfo& d, const void* fn, const cudaLaunchConfig_t* lc, int* out);
+
+inline int elem_size(int dtype) { return dtype == SR_BF16 ? 2 : (dtype == SR_FP8E4M3 ? 1 : 4); }
+
+// Single-array reduction (sr_reduce.cu)
+int reduce_validate(const void* x, int64_t n, int dtype, const void* out, const sr_config& cfg);
+int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& cfg, const DeviceInfo& d, Plan* p);
+int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, const Workspace& ws,
+                  cudaStream_t s);
+
+}  // namespace sr

@@ -1,0 +1,245 @@
+// Single-array reduction: argument validation, launch planning and launch.
+#include <algorithm>
+#include <cstring>
+
+#include "sr_internal.h"
+#include "sr_kparams.h"
+
+namespace sr {
+
+namespace {
+
+constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK;
+// Arrays up to this many bytes take the single-cluster form under SR_AUTO:
+// one launch, no grid stage (its cost is launch latency, not bandwidth).
+constexpr int64_t kAutoSingleClusterBytes = 256 << 10;
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+bool kernels_for(const Plan& p, KernelSet* k) {
+    switch (p.dtype) {
+    case SR_F32: return kernels_f32(p.comp, p.fp64, p.bulk, p.vec, p.unroll, k);
+    case SR_I32: return kernels_i32(p.comp, p.fp64, p.bulk, p.vec, p.unroll, k);
+    case SR_BF16: return kernels_bf16(p.comp, p.fp64, p.bulk, p.vec, p.unroll, k);
+    case SR_FP8E4M3: return kernels_fp8(p.comp, p.fp64, p.bulk, p.vec, p.unroll, k);
+    default: return false;
+    }
+}
+
+}  // namespace
+
+int reduce_validate(const void* x, int64_t n, int dtype, const void* out, const sr_config& c) {
+    if (dtype < SR_F32 || dtype > SR_FP8E4M3) return SR_ERR_DTYPE;
+    if (n < 0 || out == nullptr || (n > 0 && x == nullptr)) return SR_ERR_ARG;
+    const int es = elem_size(dtype);
+    if (x != nullptr && (reinterpret_cast<uintptr_t>(x) % es) != 0) return SR_ERR_ARG;
+    const bool fp64 = (c.variant & SR_F_FP64_COMBINE) && dtype != SR_I32;
+    const size_t out_align = (dtype == SR_I32 || fp64) ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(out) % out_align) return SR_ERR_ARG;
+    if (c.variant & ~kKnownFlags) return SR_ERR_ARG;
+    const int stage = c.variant & SR_STAGE_MASK;
+    const int log2c = (c.variant & SR_CLUSTER_MASK) >> SR_CLUSTER_SHIFT;
+    if (stage > SR_SINGLE_CLUSTER || log2c > 4) return SR_ERR_ARG;
+    if (c.block_threads != 0 && (c.block_threads < 32 || c.block_threads > 1024 || c.block_threads % 32))
+        return SR_ERR_ARG;
+    if ((c.variant & SR_F_BULK) && c.block_threads != 0 && c.block_threads < 64) return SR_ERR_ARG;
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32) return SR_ERR_ARG;
+    if (c.grid < 0 || c.grid > kMaxUnits) return SR_ERR_ARG;
+    if (c.vec_bytes != 0 && c.vec_bytes != 16 && c.vec_bytes != 32) return SR_ERR_ARG;
+    if (c.unroll != 0 && c.unroll != 1 && c.unroll != 2 && c.unroll != 4 && c.unroll != 8) return SR_ERR_ARG;
+    if (c.tile_bytes != 0 && (c.tile_bytes < 1024 || c.tile_bytes % 1024 || c.tile_bytes > (224 << 10)))
+        return SR_ERR_ARG;
+    if (c.stages != 0 && (c.stages < 2 || c.stages > 8)) return SR_ERR_ARG;
+    if (!(c.scale == c.scale) || c.scale < 0.f) return SR_ERR_ARG;  // NaN or negative
+    if (stage == SR_GRID_SYNC && log2c > 0) return SR_ERR_UNSUPPORTED;
+    return SR_OK;
+}
+
+int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const DeviceInfo& d, Plan* out) {
+    Plan p;
+    p.dtype = dtype;
+    p.elem = elem_size(dtype);
+    p.n = n;
+    p.comp = (c.variant & SR_F_KAHAN) && dtype != SR_I32;
+    p.fp64 = (c.variant & SR_F_FP64_COMBINE) && dtype != SR_I32;
+    p.bulk = (c.variant & SR_F_BULK) != 0;
+    p.scale = (dtype == SR_FP8E4M3 && c.scale != 0.f) ? c.scale : 1.f;
+    p.stage = c.variant & SR_STAGE_MASK;
+    p.log2c = (c.variant & SR_CLUSTER_MASK) >> SR_CLUSTER_SHIFT;
+
+    if (p.stage == SR_AUTO) {
+        if (n * p.elem <= kAutoSingleClusterBytes) {
+            p.stage = SR_SINGLE_CLUSTER;
+            if (p.log2c == 0) p.log2c = 3;
+        } else {
+            p.stage = SR_LAST_BLOCK;
+        }
+    }
+    p.cluster = 1 << p.log2c;
+
+    p.vec = p.bulk ? 16 : (c.vec_bytes ? c.vec_bytes : 16);
+    p.unroll = c.unroll ? c.unroll : 4;
+    p.block = c.block_threads ? c.block_threads : (p.bulk ? 288 : 512);
+
+    // geometry: scalar head up to the vector alignment, vector body, scalar tail
+    const int64_t per_vec = p.vec / p.elem;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(x);
+    const int64_t mis = (int64_t)(addr % (uintptr_t)p.vec);
+    p.head = mis ? std::min<int64_t>(n, (p.vec - mis) / p.elem) : 0;
+    p.nvec = (n - p.head) / per_vec;
+    p.tail_begin = p.head + p.nvec * per_vec;
+    p.ntail = n - p.tail_begin;
+
+    int ctas_per_sm;
+    int64_t work_ctas;
+    if (p.bulk) {
+        p.tile = c.tile_bytes ? c.tile_bytes : (32 << 10);
+        p.stages = c.stages ? c.stages : 6;
+        p.smem = (size_t)p.stages * p.tile + 16 * (size_t)p.stages;
+        if (p.smem > (size_t)d.smem_per_block_optin) return SR_ERR_LAUNCH;
+        p.body_bytes = p.nvec * 16;
+        p.ntiles = cdiv(p.body_bytes, p.tile);
+        const int fit = std::max(1, (int)(d.smem_per_sm / (p.smem + 2048)));
+        ctas_per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::min(fit, d.max_threads_per_sm / p.block);
+        work_ctas = std::max<int64_t>(p.ntiles, 1);
+        // the scalar head/tail are spread over consumer threads of all CTAs
+    } else {
+        ctas_per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::max(1, d.max_threads_per_sm / p.block);
+        work_ctas = std::max<int64_t>(1, cdiv(p.nvec, (int64_t)p.block * p.unroll));
+    }
+    if (!c.ctas_per_sm) {
+        // default: as many CTAs per SM as are resident at once (registers and
+        // shared memory of this kernel), so the grid is exactly one wave
+        KernelSet ks;
+        if (!kernels_for(p, &ks)) return SR_ERR_UNSUPPORTED;
+        int st = prepare_function(ks.main, p.smem, p.cluster > 8);
+        if (st != SR_OK) return st;
+        int resident = 0;
+        st = blocks_per_sm(d, ks.main, p.block, p.smem, &resident);
+        if (st != SR_OK) return st;
+        if (resident < 1) return SR_ERR_LAUNCH;
+        ctas_per_sm = std::min(ctas_per_sm, resident);
+    }
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, d.max_blocks_per_sm));
+
+    int64_t grid;
+    if (p.stage == SR_SINGLE_CLUSTER) {
+        grid = p.cluster;
+    } else if (c.grid) {
+        grid = c.grid;
+    } else {
+        grid = std::min<int64_t>((int64_t)d.sms * ctas_per_sm, work_ctas);
+    }
+    grid = cdiv(grid, p.cluster) * p.cluster;
+    if (grid / p.cluster > kMaxUnits) return SR_ERR_ARG;
+
+    if (p.stage == SR_GRID_SYNC) {
+        // A grid.sync() grid must be co-resident: size the default grid to
+        // what the occupancy calculator allows; reject an explicit grid that
+        // does not fit (Section VIII-B: partial-grid synchronisation deadlocks).
+        KernelSet ks;
+        if (!kernels_for(p, &ks)) return SR_ERR_UNSUPPORTED;
+        int st = prepare_function(ks.main, p.smem, false);
+        if (st != SR_OK) return st;
+        int per_sm = 0;
+        st = blocks_per_sm(d, ks.main, p.block, p.smem, &per_sm);
+        if (st != SR_OK) return st;
+        const int64_t cap = (int64_t)per_sm * d.sms;
+        if (!c.grid) grid = std::min(grid, cap);
+        if (grid > cap || grid < 1) return SR_ERR_LAUNCH;
+    }
+    p.grid = (int)grid;
+    p.units = p.grid / p.cluster;
+    *out = p;
+    return SR_OK;
+}
+
+int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, const Workspace& ws,
+                  cudaStream_t s) {
+    KernelSet ks;
+    if (!kernels_for(p, &ks)) return SR_ERR_UNSUPPORTED;
+
+    KParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.x = static_cast<const unsigned char*>(x);
+    kp.n = p.n;
+    kp.head = p.head;
+    kp.nvec = p.nvec;
+    kp.tail_begin = p.tail_begin;
+    kp.ntail = p.ntail;
+    kp.out = out;
+    kp.partials = ws.partials;
+    kp.ticket = ws.tickets;
+    kp.err = ws.err;
+    kp.scale = p.scale;
+    kp.stage = p.stage;
+    kp.fp64 = p.fp64 ? 1 : 0;
+    kp.units = p.units;
+    kp.log2c = p.log2c;
+    kp.tile_bytes = p.tile;
+    kp.stages = p.stages;
+    kp.body_bytes = p.body_bytes;
+    kp.ntiles = p.ntiles;
+    kp.limit_ns = spin_limit_ns();
+
+    cudaError_t e;
+    int st = prepare_function(ks.main, p.smem, p.cluster > 8);
+    if (st != SR_OK) return st;
+
+    if (p.stage == SR_ATOMIC) {
+        const size_t ob = (p.dtype == SR_I32 || p.fp64) ? 8 : 4;
+        e = cudaMemsetAsync(out, 0, ob, s);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
+
+    void* args[] = {&kp};
+    if (p.stage == SR_GRID_SYNC) {
+        // Every CTA of a grid.sync() kernel must be resident at once: check
+        // before launching rather than ever starting a grid that could wait
+        // forever (Section VIII-B: partial-grid synchronisation deadlocks).
+        int per_sm = 0;
+        st = blocks_per_sm(d, ks.main, p.block, p.smem, &per_sm);
+        if (st != SR_OK) return st;
+        if ((int64_t)per_sm * d.sms < p.grid) return SR_ERR_LAUNCH;
+        e = cudaLaunchCooperativeKernel(ks.main, dim3(p.grid), dim3(p.block), args, p.smem, s);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        return SR_OK;
+    }
+
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof lc);
+    lc.gridDim = dim3(p.grid);
+    lc.blockDim = dim3(p.block);
+    lc.dynamicSmemBytes = p.smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (p.cluster > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = p.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        int nclusters = 0;
+        st = active_clusters(d, ks.main, &lc, &nclusters);
+        if (st != SR_OK) return st;
+        if (nclusters < 1) return SR_ERR_LAUNCH;
+    }
+    e = cudaLaunchKernelExC(&lc, ks.main, args);
+    if (e != cudaSuccess) return status_from_cuda(e);
+
+    if (p.stage == SR_TWO_KERNEL) {
+        // The implicit barrier: stream order makes kernel 2 wait for every
+        // CTA of kernel 1 (Section III-B-2).
+        const int threads = std::min(1024, std::max(32, ((p.units + 31) / 32) * 32));
+        std::memset(&lc, 0, sizeof lc);
+        lc.gridDim = dim3(1);
+        lc.blockDim = dim3(threads);
+        lc.stream = s;
+        e = cudaLaunchKernelExC(&lc, ks.final, args);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
+    return SR_OK;
+}
+
+}  // namespace sr

@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads, exports every symbol include/*.h declares,
+and rejects invalid calls before touching the GPU.  No GPU needed."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2004_05371_gb300 as sr
+from paper_2004_05371_gb300 import build as sr_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sr_build.build()
+    return sr.load()
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(sr_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = _declared_symbols()
+    for required in ["sr_reduce_sum", "sr_reduce_sum_ex", "sr_stream_status", "sr_plan",
+                     "sr_status_string", "sr_last_cuda_error", "sr_version"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert sr.status_string(s).startswith("SR_")
+
+
+def _call(x, n, dtype, out, variant=0, **kw):
+    c = sr.make_config(variant, **kw)
+    return sr.reduce_sum_ptr(x, n, dtype, out, c, stream=0)
+
+
+ALIGNED = 1 << 20   # stand-in device addresses: never dereferenced on the host
+
+
+def test_rejects_bad_arguments_without_gpu(lib):
+    assert _call(ALIGNED, -1, sr.F32, ALIGNED) == sr.ERR_ARG
+    assert _call(0, 10, sr.F32, ALIGNED) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, 0) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, 7, ALIGNED) == sr.ERR_DTYPE
+    assert _call(ALIGNED + 2, 10, sr.F32, ALIGNED) == sr.ERR_ARG        # misaligned x
+    assert _call(ALIGNED, 10, sr.I32, ALIGNED + 4) == sr.ERR_ARG        # int64 out needs 8 B
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, variant=0x8000) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, variant=6) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, variant=sr.CLUSTER(5)) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, block_threads=48) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, vec_bytes=8) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, unroll=3) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, stages=9) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, tile_bytes=1000) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, grid=70000) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, scale=float("nan")) == sr.ERR_ARG
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED, variant=sr.GRID_SYNC | sr.CLUSTER(1)) == sr.ERR_UNSUPPORTED
+    # BF16 input may start on any 2-byte boundary, FP8 on any byte
+    assert _call(ALIGNED + 1, 10, sr.BF16, ALIGNED) == sr.ERR_ARG
+
+
+def test_valid_call_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert _call(ALIGNED, 10, sr.F32, ALIGNED) == sr.ERR_CUDA
+    assert _call(ALIGNED + 1, 10, sr.FP8E4M3, ALIGNED) == sr.ERR_CUDA
