@@ -13,18 +13,15 @@ own GPU (independent replicas: the path has no exchange step on one box);
 value = bytes reduced by all ranks / max-over-ranks time.
 """
 import argparse
-import ctypes
 import glob
 import hashlib
 import json
-import math
 import os
 import re
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -56,10 +53,13 @@ def _dist():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Only samples
+    whose timestamps fall inside [t_load0, t_load1] (host wall clock: the load
+    window that encloses the timed region) are reported."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -70,12 +70,22 @@ class ClockSampler:
         try:
             self.out = tempfile.TemporaryFile(mode="w+")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def _ts(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text.strip(), fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
+    def stop(self, t_load0, t_load1):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -84,15 +94,24 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.out.seek(0)
-        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        rows = [[c.strip() for c in r.split(",")] for r in self.out.read().strip().splitlines()]
+        rows = [r for r in rows if len(r) >= 10]
+        inside = [r for r in rows if (self._ts(r[0]) or 0) >= t_load0 - 0.05 and (self._ts(r[0]) or 0) <= t_load1 + 0.05]
+        use = inside or rows
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in use if num(r[2]) is not None]
+        mx = [num(r[3]) for r in use if num(r[3]) is not None]
+        pw = [num(r[4]) for r in use if num(r[4]) is not None]
+        reasons = sorted({self.REASONS[i] for r in use for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(use), "samples_in_load_window": len(inside),
+                "power_w_max": max(pw) if pw else None,
+                "window": "load window of back-to-back steps enclosing the timed region"}
 
 
 # ---------------------------------------------------------- traffic record
@@ -235,26 +254,40 @@ def main():
         step()
     torch.cuda.synchronize()
 
+    # step duration estimate, to size a ~1 s load window around the timed region
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    soak_steps = max(1, int(0.5 / max(1e-6, e0.elapsed_time(e1) / 3e3)))
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
-    # per-launch events on the launching stream (the kernel's own duration)
+    time.sleep(0.5)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    t_load0 = time.time()
+    for _ in range(soak_steps):        # untimed load before the timed region
+        step()
+    # the timed region: exactly K steps, per-launch events on the launching stream
     t_start.record(stream)
     for i in range(args.steps):
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     t_end.record(stream)
+    for _ in range(soak_steps // 2):   # untimed load after it
+        step()
     torch.cuda.synchronize()
+    t_load1 = time.time()
     if pg:
         pg.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_load0, t_load1)
     elapsed_ms = t_start.elapsed_time(t_end)
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
     if pg:

@@ -19,7 +19,10 @@ thread_local int g_last_cuda_error = 0;
 std::mutex g_mu;
 std::map<int, DeviceInfo> g_devices;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_workspaces;
-std::map<std::tuple<const void*, size_t, bool>, bool> g_prepared;
+// Per function: the largest dynamic shared memory size set so far, and
+// whether non-portable cluster sizes were enabled.  The attribute is one
+// maximum per function, so it only ever grows.
+std::map<const void*, std::pair<size_t, bool>> g_prepared;
 std::map<std::tuple<int, const void*, int, size_t>, int> g_blocks_per_sm;
 std::map<std::tuple<int, const void*, int, int, size_t>, int> g_clusters;
 
@@ -115,21 +118,19 @@ int get_workspace(cudaStream_t s, Workspace* ws) {
 }
 
 int prepare_function(const void* fn, size_t dyn_smem, bool nonportable) {
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (g_prepared.count(std::make_tuple(fn, dyn_smem, nonportable))) return SR_OK;
-    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto& st = g_prepared[fn];
     cudaError_t e;
-    if (dyn_smem > 48 * 1024) {
+    if (dyn_smem > 48 * 1024 && dyn_smem > st.first) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
         if (e != cudaSuccess) return status_from_cuda(e);
+        st.first = dyn_smem;
     }
-    if (nonportable) {
+    if (nonportable && !st.second) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return status_from_cuda(e);
+        st.second = true;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_prepared[std::make_tuple(fn, dyn_smem, nonportable)] = true;
     return SR_OK;
 }
 
