@@ -115,10 +115,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- traffic record
+KERNEL_SOURCES = ["sr_device.cuh", "sr_reduce_kernels.cuh", "sr_kparams.h", "sr_reduce_f32.cu"]
+
+
 def kernel_source_hash():
+    """Hash of the sources the single-array FP32 kernels are compiled from."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2004_05371_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2004_05371_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
