@@ -217,6 +217,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=N_HEADLINE, help="elements (profiling runs use a smaller case)")
     ap.add_argument("--skip-extras", action="store_true", help="headline loop only (profiling runs)")
+    ap.add_argument("--soak-seconds", type=float, default=0.5,
+                    help="untimed back-to-back load before the timed region (clock sampling window)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -265,10 +267,10 @@ def main():
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    soak_steps = max(1, int(0.5 / max(1e-6, e0.elapsed_time(e1) / 3e3)))
+    soak_steps = int(args.soak_seconds / max(1e-6, e0.elapsed_time(e1) / 3e3))
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.5)
+    time.sleep(0.5 if args.soak_seconds > 0 else 0.0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
