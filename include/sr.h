@@ -150,6 +150,37 @@ int sr_stream_status(sr_stream_t stream);
  * Needs a device; returns the same errors sr_reduce_sum_ex would. */
 int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
 
+/* ------------------------------------------------- allocation-free sum */
+
+/* The last-block-done sum (SR_LAST_BLOCK, LDG load path) for callers that must
+ * not allocate device memory: code running where cudaMalloc is unavailable or
+ * forbidden — inside a host function or callback that may not call the CUDA
+ * allocator, in a process whose device memory is fully reserved by another
+ * allocator, or under a policy that allows no allocation after start-up.
+ * The paper has no counterpart.
+ *
+ * Instead of the per-stream workspace it uses one file-scope device array of
+ * 64 KiB + 256 bytes (a ticket, an error word and 4096 unit-partial slots),
+ * which every GPU that loads this library holds until the process exits.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.  The caller
+ * passes x and out exactly as for sr_reduce_sum_ex.
+ *  - cfg: NULL, or a configuration whose stage is SR_AUTO or SR_LAST_BLOCK
+ *    (other stages and SR_F_BULK -> SR_ERR_UNSUPPORTED); cluster bits and the
+ *    SR_F_KAHAN / SR_F_FP64_COMBINE flags are honoured.
+ *  - At most 4096 units (CTAs, or clusters when a cluster size is set): a
+ *    larger explicit grid, or a plan needing more units, returns SR_ERR_ARG
+ *    and launches nothing.
+ *  - The first call on each device looks up the device address of the array
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents; each
+ *    call resets the ticket on `stream` before its kernel.  Calls whose work
+ *    overlaps on the GPU (different streams, no ordering between them) race on
+ *    the array and give wrong results: order them on one stream.
+ * Errors: as sr_reduce_sum_ex. */
+int sr_reduce_sum_noalloc(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg,
+                          sr_stream_t stream);
+
 /* ------------------------------------------------------ host helpers */
 
 const char* sr_status_string(int status);

@@ -69,6 +69,8 @@ def load():
     L.sr_reduce_sum.argtypes = [vp, i64, i32, vp, i32, vp]
     L.sr_reduce_sum_ex.restype = i32
     L.sr_reduce_sum_ex.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
+    L.sr_reduce_sum_noalloc.restype = i32
+    L.sr_reduce_sum_noalloc.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -138,6 +140,14 @@ def reduce_sum_ptr(x_ptr: int, n: int, dtype: int, out_ptr: int, config: Config 
     cfg = ctypes.byref(config) if config is not None else None
     return lib().sr_reduce_sum_ex(ctypes.c_void_p(x_ptr), int(n), int(dtype), ctypes.c_void_p(out_ptr), cfg,
                                   ctypes.c_void_p(_stream(stream)))
+
+
+def reduce_sum_noalloc_ptr(x_ptr: int, n: int, dtype: int, out_ptr: int, config: Config = None,
+                           stream=None) -> int:
+    """Raw call of sr_reduce_sum_noalloc (no device allocation); returns the status."""
+    cfg = ctypes.byref(config) if config is not None else None
+    return lib().sr_reduce_sum_noalloc(ctypes.c_void_p(x_ptr), int(n), int(dtype), ctypes.c_void_p(out_ptr), cfg,
+                                       ctypes.c_void_p(_stream(stream)))
 
 
 def reduce_sum(x, variant: int = AUTO, out=None, config: Config = None, stream=None, **cfg_fields):

@@ -1,0 +1,48 @@
+"""sr_reduce_sum_noalloc: the sum for callers that cannot allocate device
+memory (no cudaMalloc available or allowed where they run).  It keeps its
+scratch in one fixed device array inside the library instead of a workspace
+allocated on first use.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+ALIGNED = 1 << 20   # stand-in device address: never dereferenced on the host
+
+
+def test_noalloc_rejects_without_touching_the_gpu(sr):
+    def call(**kw):
+        return sr.reduce_sum_noalloc_ptr(ALIGNED, 1000, sr.F32, ALIGNED, sr.make_config(**kw), stream=0)
+    assert call(variant=sr.TWO_KERNEL) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.ATOMIC) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.F_BULK) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK, grid=4097) == sr.ERR_ARG          # above the 4096-unit maximum
+    assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1), grid=8194) == sr.ERR_ARG
+    assert sr.reduce_sum_noalloc_ptr(ALIGNED, -1, sr.F32, ALIGNED, None, stream=0) == sr.ERR_ARG
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_allocating_entry_point(sr):
+    """Two calls in a row through the C ABI agree with sr_reduce_sum_ex's
+    last-block-done result: within the FP32 gate the parity tests use for
+    binary32 input, exactly for int32 input."""
+    import torch
+    cases = [(workloads.uniform_f32((1 << 20) + 3, seed=21), sr.F32),
+             (workloads.uniform_f32(1 << 24, seed=22), sr.F32),
+             (workloads.uniform_i32((1 << 22) + 1, seed=23), sr.I32)]
+    for x_np, dt in cases:
+        x = torch.from_numpy(x_np).cuda()
+        odt = torch.int64 if dt == sr.I32 else torch.float32
+        ref = torch.empty((), dtype=odt, device="cuda")
+        sr.check(sr.reduce_sum_ptr(x.data_ptr(), x.numel(), dt, ref.data_ptr(), sr.make_config(sr.LAST_BLOCK)))
+        for _ in range(2):
+            out = torch.full((), -7, dtype=odt, device="cuda")
+            sr.check(sr.reduce_sum_noalloc_ptr(x.data_ptr(), x.numel(), dt, out.data_ptr(), None))
+            torch.cuda.synchronize()
+            if dt == sr.I32:
+                assert int(out.item()) == int(ref.item()) == oracle.sum_i32(x_np)
+            else:
+                bound = oracle.stated_fp32_bound(oracle.sum_abs_f32(x_np))
+                assert abs(float(out.item()) - float(ref.item())) <= bound
+                assert abs(float(out.item()) - oracle.to_float(oracle.exact_f32(x_np))) <= bound
