@@ -150,6 +150,46 @@ int sr_stream_status(sr_stream_t stream);
  * Needs a device; returns the same errors sr_reduce_sum_ex would. */
 int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
 
+/* ------------------------------------------------------ segmented sum */
+
+/* Batched sum over CSR segments: out[s] = sum x[offsets[s] .. offsets[s+1])
+ * for s < nseg — the paper's reduction (Section VII) applied to many arrays
+ * in one launch.  x: device array (element-aligned) holding at least
+ * offsets[nseg] elements; offsets: device int64 array of nseg + 1 entries,
+ * non-decreasing (the caller guarantees it; it is not checked); out: device
+ * array of nseg results (int64 for SR_I32, float, or double with
+ * SR_F_FP64_COMBINE).  Empty segments give 0.  nseg == 0 launches nothing.
+ * The concatenated range is split evenly over the warps of one persistent
+ * grid whatever the segment lengths; segments crossing a warp boundary are
+ * finished by the configured grid stage: SR_TWO_KERNEL, SR_GRID_SYNC,
+ * SR_LAST_BLOCK (default; per-segment tickets) or SR_ATOMIC (out zeroed
+ * first; FP order not deterministic).  All other forms are deterministic.
+ * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE),
+ * block_threads, ctas_per_sm, grid (at most 65536 warps in total), vec_bytes,
+ * unroll, scale (FP8).  SR_SINGLE_CLUSTER, cluster bits and SR_F_BULK ->
+ * SR_ERR_UNSUPPORTED.
+ * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,
+ * bad config), SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
+int sr_reduce_sum_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                            sr_stream_t stream);
+int sr_reduce_sum_segmented_ex(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                               const sr_config* cfg, sr_stream_t stream);
+
+/* Resolved launch shape of a segmented call (as sr_plan).  Needs a device. */
+int sr_plan_segmented(int64_t nseg, int dtype, const sr_config* cfg, sr_config* resolved);
+
+/* A segmented sum captured once into a CUDA graph owned by the library and
+ * replayed with one graph launch (no per-call host work).  The pointers are
+ * baked into the graph: x, offsets and out must stay valid and keep their
+ * addresses until sr_graph_destroy.  The graph has its own workspace (created
+ * at capture time), so replays must not overlap each other on the GPU.
+ * Capture errors: as sr_reduce_sum_segmented_ex, nseg == 0 -> SR_ERR_ARG. */
+typedef struct sr_graph_s* sr_graph;
+int sr_graph_capture_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                               const sr_config* cfg, sr_graph* graph);
+int sr_graph_launch(sr_graph graph, sr_stream_t stream);
+int sr_graph_destroy(sr_graph graph);
+
 /* ------------------------------------------------- allocation-free sum */
 
 /* The last-block-done sum (SR_LAST_BLOCK, LDG load path) for callers that must

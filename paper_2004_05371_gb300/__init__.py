@@ -71,6 +71,18 @@ def load():
     L.sr_reduce_sum_ex.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
     L.sr_reduce_sum_noalloc.restype = i32
     L.sr_reduce_sum_noalloc.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
+    L.sr_reduce_sum_segmented.restype = i32
+    L.sr_reduce_sum_segmented.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.sr_reduce_sum_segmented_ex.restype = i32
+    L.sr_reduce_sum_segmented_ex.argtypes = [vp, vp, i64, i32, vp, ctypes.POINTER(Config), vp]
+    L.sr_plan_segmented.restype = i32
+    L.sr_plan_segmented.argtypes = [i64, i32, ctypes.POINTER(Config), ctypes.POINTER(Config)]
+    L.sr_graph_capture_segmented.restype = i32
+    L.sr_graph_capture_segmented.argtypes = [vp, vp, i64, i32, vp, ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    L.sr_graph_launch.restype = i32
+    L.sr_graph_launch.argtypes = [vp, vp]
+    L.sr_graph_destroy.restype = i32
+    L.sr_graph_destroy.argtypes = [vp]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -167,6 +179,70 @@ def reduce_sum(x, variant: int = AUTO, out=None, config: Config = None, stream=N
     st = reduce_sum_ptr(x.data_ptr(), x.numel(), dt, out.data_ptr(), config, stream)
     check(st, "sr_reduce_sum_ex")
     return out
+
+
+def reduce_sum_segmented_ptr(x_ptr: int, offsets_ptr: int, nseg: int, dtype: int, out_ptr: int,
+                             config: Config = None, stream=None) -> int:
+    """Raw call of sr_reduce_sum_segmented_ex; returns the status (no raise)."""
+    cfg = ctypes.byref(config) if config is not None else None
+    return lib().sr_reduce_sum_segmented_ex(ctypes.c_void_p(x_ptr), ctypes.c_void_p(offsets_ptr), int(nseg),
+                                            int(dtype), ctypes.c_void_p(out_ptr), cfg,
+                                            ctypes.c_void_p(_stream(stream)))
+
+
+def reduce_sum_segmented(x, offsets, variant: int = AUTO, out=None, config: Config = None, stream=None,
+                         **cfg_fields):
+    """Per-segment sums of a CUDA tensor over int64 CSR offsets (CUDA tensor of
+    nseg + 1 entries).  Returns a CUDA tensor of nseg results."""
+    import torch
+    if not (x.is_cuda and offsets.is_cuda and x.is_contiguous() and offsets.is_contiguous()):
+        raise ValueError("x and offsets must be contiguous CUDA tensors")
+    if offsets.dtype != torch.int64:
+        raise TypeError("offsets must be int64")
+    dt = dtype_code(x)
+    if config is None:
+        config = make_config(variant, **cfg_fields)
+    nseg = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(max(nseg, 0), dtype=out_dtype(dt, config.variant), device=x.device)
+    st = reduce_sum_segmented_ptr(x.data_ptr(), offsets.data_ptr(), nseg, dt, out.data_ptr(), config, stream)
+    check(st, "sr_reduce_sum_segmented_ex")
+    return out
+
+
+def plan_segmented(nseg: int, dtype: int, config: Config = None) -> Config:
+    r = Config()
+    cfg = ctypes.byref(config) if config is not None else None
+    check(lib().sr_plan_segmented(int(nseg), int(dtype), cfg, ctypes.byref(r)), "sr_plan_segmented")
+    return r
+
+
+class SegmentedGraph:
+    """A segmented sum captured once into a library-owned CUDA graph
+    (sr_graph_capture_segmented); launch() replays it with one graph launch.
+    The tensors must stay alive (and in place) until close()."""
+
+    def __init__(self, x, offsets, out, config: Config = None):
+        self._keep = (x, offsets, out)
+        self._h = ctypes.c_void_p()
+        cfg = ctypes.byref(config) if config is not None else None
+        check(lib().sr_graph_capture_segmented(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(offsets.data_ptr()),
+                                               offsets.numel() - 1, dtype_code(x), ctypes.c_void_p(out.data_ptr()),
+                                               cfg, ctypes.byref(self._h)), "sr_graph_capture_segmented")
+
+    def launch(self, stream=None):
+        check(lib().sr_graph_launch(self._h, ctypes.c_void_p(_stream(stream))), "sr_graph_launch")
+
+    def close(self):
+        if self._h:
+            lib().sr_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def plan(n: int, dtype: int, config: Config = None) -> Config:

@@ -117,6 +117,16 @@ int get_workspace(cudaStream_t s, Workspace* ws) {
     return SR_OK;
 }
 
+void release_workspace(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_workspaces.find(std::make_pair(dev, s));
+    if (it == g_workspaces.end()) return;
+    cudaFree(it->second.base);
+    g_workspaces.erase(it);
+}
+
 int prepare_function(const void* fn, size_t dyn_smem, bool nonportable) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto& st = g_prepared[fn];
@@ -208,6 +218,116 @@ int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out, const sr_co
 int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant, sr_stream_t stream) {
     const sr_config c = default_config(variant);
     return sr_reduce_sum_ex(x, n, dtype, out, &c, stream);
+}
+
+int sr_reduce_sum_segmented_ex(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                               const sr_config* cfg, sr_stream_t stream) {
+    const sr_config c = cfg ? *cfg : default_config(SR_AUTO);
+    int st = seg_validate(x, offsets, nseg, dtype, out, c);
+    if (st != SR_OK) return st;
+    if (nseg == 0) return SR_OK;
+    const DeviceInfo* d = current_device(&st);
+    if (!d) return st;
+    SegPlan p;
+    st = seg_plan(nseg, dtype, c, *d, &p);
+    if (st != SR_OK) return st;
+    Workspace ws;
+    st = get_workspace((cudaStream_t)stream, &ws);
+    if (st != SR_OK) return st;
+    return seg_launch(x, offsets, out, p, ws, (cudaStream_t)stream);
+}
+
+int sr_reduce_sum_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                            sr_stream_t stream) {
+    return sr_reduce_sum_segmented_ex(x, offsets, nseg, dtype, out, nullptr, stream);
+}
+
+int sr_plan_segmented(int64_t nseg, int dtype, const sr_config* cfg, sr_config* resolved) {
+    if (!resolved) return SR_ERR_ARG;
+    const sr_config c = cfg ? *cfg : default_config(SR_AUTO);
+    const void* fake = reinterpret_cast<const void*>(uintptr_t(1) << 20);
+    int st = seg_validate(fake, reinterpret_cast<const int64_t*>(fake), nseg, dtype, fake, c);
+    if (st != SR_OK) return st;
+    const DeviceInfo* d = current_device(&st);
+    if (!d) return st;
+    SegPlan p;
+    st = seg_plan(nseg, dtype, c, *d, &p);
+    if (st != SR_OK) return st;
+    sr_config r = c;
+    r.variant = (c.variant & ~SR_STAGE_MASK) | p.stage;
+    r.block_threads = p.block;
+    r.grid = p.grid;
+    r.vec_bytes = p.vec;
+    r.unroll = p.unroll;
+    r.scale = p.scale;
+    *resolved = r;
+    return SR_OK;
+}
+
+struct sr_graph_s {
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int sr_graph_capture_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                               const sr_config* cfg, sr_graph* g) {
+    if (!g) return SR_ERR_ARG;
+    *g = nullptr;
+    const sr_config c = cfg ? *cfg : default_config(SR_AUTO);
+    int st = seg_validate(x, offsets, nseg, dtype, out, c);
+    if (st != SR_OK) return st;
+    if (nseg == 0) return SR_ERR_ARG;
+    const DeviceInfo* d = current_device(&st);
+    if (!d) return st;
+    SegPlan p;
+    st = seg_plan(nseg, dtype, c, *d, &p);
+    if (st != SR_OK) return st;
+    sr_graph h = new sr_graph_s;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return status_from_cuda(e);
+    }
+    Workspace ws;
+    st = get_workspace(h->capture_stream, &ws);  // allocated before capture begins
+    if (st == SR_OK) {
+        e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = status_from_cuda(e);
+    }
+    if (st == SR_OK) {
+        int lst = seg_launch(x, offsets, out, p, ws, h->capture_stream);
+        e = cudaStreamEndCapture(h->capture_stream, &h->graph);
+        st = lst != SR_OK ? lst : (e != cudaSuccess ? status_from_cuda(e) : SR_OK);
+    }
+    if (st == SR_OK) {
+        e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+        if (e != cudaSuccess) st = status_from_cuda(e);
+    }
+    if (st != SR_OK) {
+        sr_graph_destroy(h);
+        return st;
+    }
+    *g = h;
+    return SR_OK;
+}
+
+int sr_graph_launch(sr_graph g, sr_stream_t stream) {
+    if (!g || !g->exec) return SR_ERR_ARG;
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? SR_OK : status_from_cuda(e);
+}
+
+int sr_graph_destroy(sr_graph g) {
+    if (!g) return SR_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->capture_stream) {
+        release_workspace(g->capture_stream);
+        cudaStreamDestroy(g->capture_stream);
+    }
+    delete g;
+    return SR_OK;
 }
 
 int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved) {

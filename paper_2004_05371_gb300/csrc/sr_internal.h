@@ -18,6 +18,9 @@ namespace sr {
 constexpr int kMaxUnits = 65536;
 constexpr size_t kSlotBytes = 16;
 constexpr size_t kSegBytes = 4u << 20;
+// Segmented carries: tickets (4 B), last_seg (8 B), carry_first and
+// carry_last (16 B each) per warp: 44 B x 65536 warps = 2.75 MiB <= kSegBytes.
+constexpr int64_t kSegMaxWarps = 65536;
 constexpr size_t kHeaderBytes = 256;
 
 struct Workspace {
@@ -55,10 +58,24 @@ struct Plan {
     int64_t body_bytes = 0, ntiles = 0;
 };
 
+// A resolved segmented launch.
+struct SegPlan {
+    int dtype = 0;
+    int64_t nseg = 0;
+    int stage = 0;
+    bool comp = false, fp64 = false;
+    int vec = 16, unroll = 4, block = 256, grid = 0;
+    int64_t warps = 0;
+    float scale = 1.f;
+    const void* main = nullptr;
+    const void* fin = nullptr;
+};
+
 // C-ABI layer services
 int status_from_cuda(cudaError_t e);           // records the error, returns SR_ERR_CUDA
 const DeviceInfo* current_device(int* status);  // cached per device
 int get_workspace(cudaStream_t s, Workspace* ws);
+void release_workspace(cudaStream_t s);  // frees the workspace of (current device, s)
 uint64_t spin_limit_ns();
 
 // Cached per-function launch facts (one query per function and shape).
@@ -73,5 +90,12 @@ int reduce_validate(const void* x, int64_t n, int dtype, const void* out, const 
 int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& cfg, const DeviceInfo& d, Plan* p);
 int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, const Workspace& ws,
                   cudaStream_t s);
+
+// Segmented sum (sr_segmented.cu)
+int seg_validate(const void* x, const int64_t* offsets, int64_t nseg, int dtype, const void* out,
+                 const sr_config& cfg);
+int seg_plan(int64_t nseg, int dtype, const sr_config& cfg, const DeviceInfo& d, SegPlan* p);
+int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& p, const Workspace& ws,
+               cudaStream_t s);
 
 }  // namespace sr

@@ -31,6 +31,28 @@ struct KParams {
     uint64_t limit_ns;        // bound on every device-side wait
 };
 
+// Kernel argument block of the segmented sum (sr_segmented_kernels.cuh).
+struct SegParams {
+    const unsigned char* x;
+    const int64_t* offsets;     // nseg + 1 entries, non-decreasing
+    int64_t nseg;
+    void* out;                  // nseg results
+    unsigned char* carry_first; // W slots of 16 bytes (W = warps of the grid)
+    unsigned char* carry_last;  // W slots of 16 bytes
+    int64_t* last_seg;          // W entries: owned spanning segment or -1
+    unsigned int* cnt;          // W self-resetting tickets (last-block form)
+    int* err;
+    float scale;
+    int stage;
+    int fp64;
+};
+
+// Per-dtype segmented kernel selection.
+bool seg_kernels_f32(bool comp, int vec, int unroll, const void** main, const void** fin);
+bool seg_kernels_i32(bool comp, int vec, int unroll, const void** main, const void** fin);
+bool seg_kernels_bf16(bool comp, int vec, int unroll, const void** main, const void** fin);
+bool seg_kernels_fp8(bool comp, int vec, int unroll, const void** main, const void** fin);
+
 struct KernelSet {
     const void* main = nullptr;   // thread..grid stages
     const void* final = nullptr;  // second kernel of the two-kernel form

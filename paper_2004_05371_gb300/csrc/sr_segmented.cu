@@ -1,0 +1,120 @@
+// Segmented sum: validation, launch planning and launch (C ABI in sr_api.cu).
+#include <algorithm>
+#include <cstring>
+
+#include "sr_internal.h"
+#include "sr_kparams.h"
+
+namespace sr {
+
+namespace {
+constexpr int kKnownSegFlags = SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE;
+
+bool seg_kernels(int dtype, bool comp, int vec, int unroll, const void** main, const void** fin) {
+    switch (dtype) {
+    case SR_F32: return seg_kernels_f32(comp, vec, unroll, main, fin);
+    case SR_I32: return seg_kernels_i32(comp, vec, unroll, main, fin);
+    case SR_BF16: return seg_kernels_bf16(comp, vec, unroll, main, fin);
+    case SR_FP8E4M3: return seg_kernels_fp8(comp, vec, unroll, main, fin);
+    default: return false;
+    }
+}
+}  // namespace
+
+int seg_validate(const void* x, const int64_t* offsets, int64_t nseg, int dtype, const void* out,
+                 const sr_config& c) {
+    if (dtype < SR_F32 || dtype > SR_FP8E4M3) return SR_ERR_DTYPE;
+    if (nseg < 0) return SR_ERR_ARG;
+    if (nseg > 0 && (x == nullptr || offsets == nullptr || out == nullptr)) return SR_ERR_ARG;
+    if (x && reinterpret_cast<uintptr_t>(x) % elem_size(dtype)) return SR_ERR_ARG;
+    if (offsets && reinterpret_cast<uintptr_t>(offsets) % 8) return SR_ERR_ARG;
+    const bool fp64 = (c.variant & SR_F_FP64_COMBINE) && dtype != SR_I32;
+    if (out && reinterpret_cast<uintptr_t>(out) % ((dtype == SR_I32 || fp64) ? 8 : 4)) return SR_ERR_ARG;
+    if (c.variant & ~kKnownSegFlags) return (c.variant & (SR_F_BULK | SR_CLUSTER_MASK)) ? SR_ERR_UNSUPPORTED
+                                                                                           : SR_ERR_ARG;
+    const int stage = c.variant & SR_STAGE_MASK;
+    if (stage > SR_SINGLE_CLUSTER) return SR_ERR_ARG;
+    if (stage == SR_SINGLE_CLUSTER) return SR_ERR_UNSUPPORTED;
+    if (c.block_threads != 0 && (c.block_threads < 32 || c.block_threads > 1024 || c.block_threads % 32))
+        return SR_ERR_ARG;
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32) return SR_ERR_ARG;
+    if (c.grid < 0) return SR_ERR_ARG;
+    if (c.vec_bytes != 0 && c.vec_bytes != 16 && c.vec_bytes != 32) return SR_ERR_ARG;
+    if (c.unroll != 0 && c.unroll != 1 && c.unroll != 2 && c.unroll != 4 && c.unroll != 8) return SR_ERR_ARG;
+    if (!(c.scale == c.scale) || c.scale < 0.f) return SR_ERR_ARG;
+    const int block = c.block_threads ? c.block_threads : 256;
+    if ((int64_t)c.grid * (block / 32) > kSegMaxWarps) return SR_ERR_ARG;
+    return SR_OK;
+}
+
+int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, SegPlan* out) {
+    SegPlan p;
+    p.dtype = dtype;
+    p.nseg = nseg;
+    p.comp = (c.variant & SR_F_KAHAN) && dtype != SR_I32;
+    p.fp64 = (c.variant & SR_F_FP64_COMBINE) && dtype != SR_I32;
+    p.stage = c.variant & SR_STAGE_MASK;
+    if (p.stage == SR_AUTO) p.stage = SR_LAST_BLOCK;
+    p.vec = c.vec_bytes ? c.vec_bytes : 16;
+    p.unroll = c.unroll ? c.unroll : 4;
+    p.block = c.block_threads ? c.block_threads : 256;
+    p.scale = (dtype == SR_FP8E4M3 && c.scale != 0.f) ? c.scale : 1.f;
+    if (!seg_kernels(dtype, p.comp, p.vec, p.unroll, &p.main, &p.fin)) return SR_ERR_UNSUPPORTED;
+    int resident = 0;
+    int st = blocks_per_sm(d, p.main, p.block, 0, &resident);
+    if (st != SR_OK) return st;
+    if (resident < 1) return SR_ERR_LAUNCH;
+    int per_sm = c.ctas_per_sm ? std::min(c.ctas_per_sm, resident) : resident;
+    int64_t grid = c.grid ? c.grid : (int64_t)d.sms * per_sm;
+    grid = std::min<int64_t>(grid, kSegMaxWarps / (p.block / 32));
+    if (p.stage == SR_GRID_SYNC && grid > (int64_t)resident * d.sms) {
+        if (c.grid) return SR_ERR_LAUNCH;  // cannot be co-resident: never launched
+        grid = (int64_t)resident * d.sms;
+    }
+    p.grid = (int)std::max<int64_t>(1, grid);
+    p.warps = (int64_t)p.grid * (p.block / 32);
+    *out = p;
+    return SR_OK;
+}
+
+int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& p, const Workspace& ws,
+               cudaStream_t s) {
+    SegParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.x = static_cast<const unsigned char*>(x);
+    kp.offsets = offsets;
+    kp.nseg = p.nseg;
+    kp.out = out;
+    kp.cnt = reinterpret_cast<unsigned int*>(ws.seg);
+    kp.last_seg = reinterpret_cast<int64_t*>(ws.seg + (size_t)kSegMaxWarps * 4);
+    kp.carry_first = ws.seg + (size_t)kSegMaxWarps * 12;
+    kp.carry_last = ws.seg + (size_t)kSegMaxWarps * 28;
+    kp.err = ws.err;
+    kp.scale = p.scale;
+    kp.stage = p.stage;
+    kp.fp64 = p.fp64 ? 1 : 0;
+    cudaError_t e;
+    if (p.stage == SR_ATOMIC) {
+        const size_t ob = (p.dtype == SR_I32 || p.fp64) ? 8 : 4;
+        e = cudaMemsetAsync(out, 0, ob * (size_t)p.nseg, s);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
+    void* args[] = {&kp};
+    if (p.stage == SR_GRID_SYNC) {
+        e = cudaLaunchCooperativeKernel(p.main, dim3(p.grid), dim3(p.block), args, 0, s);
+    } else {
+        e = cudaLaunchKernel(p.main, dim3(p.grid), dim3(p.block), args, 0, s);
+    }
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (p.stage == SR_TWO_KERNEL) {
+        int64_t wn = p.warps;
+        int pv = p.vec / elem_size(p.dtype);
+        void* fargs[] = {&kp, &wn, &pv};
+        const int fblocks = (int)((p.warps * 32 + 255) / 256);
+        e = cudaLaunchKernel(p.fin, dim3(fblocks), dim3(256), fargs, 0, s);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
+    return SR_OK;
+}
+
+}  // namespace sr

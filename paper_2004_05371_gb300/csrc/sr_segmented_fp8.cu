@@ -1,0 +1,9 @@
+// Segmented-sum kernel instantiations for one input dtype.
+#include "sr_segmented_kernels.cuh"
+
+namespace sr {
+bool seg_kernels_fp8(bool comp, int vec, int unroll, const void** main, const void** fin) {
+    return comp ? pick_seg_kernels<kDtFP8, true>(vec, unroll, main, fin)
+                : pick_seg_kernels<kDtFP8, false>(vec, unroll, main, fin);
+}
+}  // namespace sr

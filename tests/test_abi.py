@@ -82,3 +82,21 @@ def test_valid_call_without_gpu_reports_cuda_error(lib):
         pytest.skip("a GPU is present")
     assert _call(ALIGNED, 10, sr.F32, ALIGNED) == sr.ERR_CUDA
     assert _call(ALIGNED + 1, 10, sr.FP8E4M3, ALIGNED) == sr.ERR_CUDA
+
+
+def test_segmented_rejects_bad_arguments_without_gpu(lib):
+    def call(nseg=4, dtype=sr.F32, x=ALIGNED, off=ALIGNED, out=ALIGNED, **kw):
+        return sr.reduce_sum_segmented_ptr(x, off, nseg, dtype, out, sr.make_config(**kw), stream=0)
+    assert call(nseg=-1) == sr.ERR_ARG
+    assert call(x=0) == sr.ERR_ARG
+    assert call(off=0) == sr.ERR_ARG
+    assert call(out=0) == sr.ERR_ARG
+    assert call(dtype=9) == sr.ERR_DTYPE
+    assert call(off=ALIGNED + 4) == sr.ERR_ARG                     # offsets need 8-byte alignment
+    assert call(dtype=sr.I32, out=ALIGNED + 4) == sr.ERR_ARG       # int64 results need 8 bytes
+    assert call(variant=sr.SINGLE_CLUSTER) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.F_BULK) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1)) == sr.ERR_UNSUPPORTED
+    assert call(block_threads=100) == sr.ERR_ARG
+    assert call(grid=100000, block_threads=1024) == sr.ERR_ARG     # more than 65536 warps
+    assert call(nseg=0, x=0, off=0, out=0) == sr.OK                 # nothing to do, nothing launched

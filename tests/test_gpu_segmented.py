@@ -1,0 +1,170 @@
+"""Parity of the segmented (batched) sum with the CPU oracle, segment by segment.
+
+int32: bit-exact per segment.  binary32 (random-sign data): per segment
+|err| <= 4 eps32 sum|x_seg| (the stated plain-tree gate), and within the
+compensated bound with SR_F_KAHAN.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+STAGES = [1, 2, 3, 4]  # two-kernel, atomic, last-block, grid-sync
+EPS32 = 2.0 ** -23
+U = 2.0 ** -24
+
+
+def _dev(a, offset=0):
+    buf = torch.zeros(a.size + offset + 8, dtype=torch.from_numpy(a[:0]).dtype, device="cuda")
+    v = buf[offset:offset + a.size]
+    if a.size:
+        v.copy_(torch.from_numpy(a))
+    return v
+
+
+def _check(sr, x, off, variant, x_off=0, **cfg):
+    """Run one segmented call and compare every segment with the oracle."""
+    xd = _dev(x, x_off)
+    od = torch.from_numpy(off).cuda()
+    out = sr.reduce_sum_segmented(xd, od, config=sr.make_config(variant, **cfg))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    if x.dtype == np.int32:
+        ref = oracle.segsum_i32(x, off)
+        bad = np.nonzero(got != ref)[0]
+        assert bad.size == 0, (variant, cfg, bad[:5], got[bad[:5]], ref[bad[:5]])
+    else:
+        ex = oracle.segexact_f32(x, off)
+        sabs = oracle.segsum_abs_f32(x, off)
+        tol = (2 * U + np.diff(off) * U * U) * sabs if variant & sr.F_KAHAN else 4 * EPS32 * sabs
+        err = np.abs(got.astype(np.float64) - ex)
+        bad = np.nonzero(err > tol)[0]
+        assert bad.size == 0, (variant, cfg, bad[:5], got[bad[:5]], ex[bad[:5]])
+    return got
+
+
+@pytest.mark.parametrize("stage", STAGES)
+@pytest.mark.parametrize("nseg,max_len", [(1, 0), (1, 1), (1, 100_000), (2, 5), (31, 0), (33, 7),
+                                          (500, 300), (5000, 40), (300, 20_000)])
+def test_random_layouts(sr, stage, nseg, max_len):
+    off = workloads.random_segment_offsets(nseg, max_len, seed=nseg + max_len)
+    n = int(off[-1])
+    xf = workloads.uniform_f32(n, seed=1)
+    xi = workloads.uniform_i32(n, seed=1)
+    for grid in (0, 1, 3):
+        for x_off in (0, 1):
+            _check(sr, xi, off, stage, x_off, grid=grid)
+            _check(sr, xf, off, stage, x_off, grid=grid)
+
+
+@pytest.mark.parametrize("stage", STAGES)
+@pytest.mark.parametrize("vec,unroll,block", [(16, 1, 32), (16, 4, 256), (32, 2, 512), (32, 8, 1024), (16, 8, 128)])
+def test_launch_shapes(sr, stage, vec, unroll, block):
+    off = workloads.segment_offsets(300, 1 << 20, seed=5, median=1024, sigma=2.0, hi=1 << 18)
+    n = int(off[-1])
+    _check(sr, workloads.uniform_i32(n, seed=2), off, stage, vec_bytes=vec, unroll=unroll, block_threads=block)
+    _check(sr, workloads.uniform_f32(n, seed=2), off, stage, 3, vec_bytes=vec, unroll=unroll, block_threads=block)
+
+
+def test_base_offset_and_trailing_empty_segments(sr):
+    off = np.array([5, 5, 9, 9, 100, 1000, 1000, 1000], dtype=np.int64)
+    x = workloads.uniform_i32(1000, seed=3)
+    for st in STAGES:
+        for grid in (0, 1, 2, 64):
+            _check(sr, x, off, st, grid=grid)
+
+
+def test_all_empty_and_single_element_segments(sr):
+    off = np.zeros(1001, np.int64)
+    x = np.zeros(0, np.int32)
+    for st in STAGES:
+        got = _check(sr, np.zeros(1, np.int32), off, st)
+        assert not got.any()
+    off = np.arange(100_001, dtype=np.int64)
+    x = workloads.uniform_i32(100_000, seed=4)
+    for st in STAGES:
+        got = _check(sr, x, off, st)
+        assert np.array_equal(got, x.astype(np.int64))
+
+
+def test_one_segment_spans_every_warp(sr):
+    n = (1 << 22) + 3
+    off = np.array([0, n], np.int64)
+    x = workloads.uniform_f32(n, seed=6)
+    xi = workloads.uniform_i32(n, seed=6)
+    for st in STAGES:
+        _check(sr, xi, off, st)
+        _check(sr, x, off, st)
+    off3 = np.array([0, 1, n - 1, n], np.int64)
+    for st in STAGES:
+        _check(sr, xi, off3, st)
+
+
+@pytest.mark.parametrize("flags", [0x100, 0x300, 0x200])
+def test_precision_flags(sr, flags):
+    off = workloads.segment_offsets(2000, 1 << 21, seed=8, median=512, sigma=2.0, hi=1 << 19)
+    x = workloads.lognormal_f32(int(off[-1]), seed=8, sigma=3.0)
+    for st in STAGES:
+        _check(sr, x, off, st | flags)
+
+
+def test_bf16_and_fp8_segments(sr):
+    off = workloads.random_segment_offsets(700, 3000, seed=9)
+    n = int(off[-1])
+    x = workloads.lognormal_f32(n, seed=9, sigma=2.0)
+    bits = workloads.to_bf16_bits(x)
+    codes, deq = workloads.to_e4m3_codes(x)
+    od = torch.from_numpy(off).cuda()
+    dec_b = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+    xd_b = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    xd_f = torch.from_numpy(codes).cuda()
+    dec_f = (torch.from_numpy(codes).view(torch.float8_e4m3fn).float() * deq).numpy()
+    for st in STAGES:
+        got = sr.reduce_sum_segmented(xd_b, od, variant=st).cpu().numpy()
+        ex = oracle.segexact_f32(dec_b, off)
+        assert np.all(np.abs(got - ex) <= 4 * EPS32 * oracle.segsum_abs_f32(dec_b, off) + 1e-30)
+        got = sr.reduce_sum_segmented(xd_f, od, config=sr.make_config(st, scale=deq)).cpu().numpy()
+        for s in range(0, 700, 37):
+            a, b = off[s], off[s + 1]
+            exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
+            sabs = float(np.abs(dec_f[a:b]).astype(np.float64).sum())
+            assert abs(got[s] - exs) <= 4 * EPS32 * sabs * 1.001 + 1e-30
+
+
+def test_deterministic_and_graph_replay(sr):
+    off = workloads.segment_offsets(3000, 1 << 22, seed=10, median=512, sigma=2.0, hi=1 << 20)
+    n = int(off[-1])
+    x = workloads.uniform_f32(n, seed=10)
+    xd, od = _dev(x), torch.from_numpy(off).cuda()
+    for st in (1, 3, 4):
+        outs = [sr.reduce_sum_segmented(xd, od, variant=st).cpu().numpy() for _ in range(3)]
+        assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    ref = sr.reduce_sum_segmented(xd, od, variant=sr.LAST_BLOCK).cpu().numpy()
+    out = torch.full((off.size - 1,), -1.0, dtype=torch.float32, device="cuda")
+    g = sr.SegmentedGraph(xd, od, out, sr.make_config(sr.LAST_BLOCK))
+    for _ in range(3):
+        out.fill_(-1.0)
+        g.launch()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
+    g.close()
+    assert sr.stream_status() == sr.OK
+
+
+@pytest.mark.slow
+def test_full_size_lognormal_10k_segments(sr):
+    """10,000 segments, lengths lognormal (median 4096, sigma 1.94, clipped to
+    [1, 2^24]), about 2^28 elements: every segment against the oracle."""
+    off = workloads.segment_offsets(10_000, 1 << 28, seed=0)
+    n = int(off[-1])
+    x = workloads.uniform_f32(n, seed=0)
+    xd, od = _dev(x), torch.from_numpy(off).cuda()
+    ex = oracle.segexact_f32(x, off)
+    tol = 4 * EPS32 * oracle.segsum_abs_f32(x, off)
+    for st in STAGES:
+        got = sr.reduce_sum_segmented(xd, od, variant=st).cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - ex) <= tol), st
