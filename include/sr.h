@@ -107,7 +107,9 @@ typedef enum {
     SR_LEVEL_GRID = 4,       /* cooperative grid.sync() */
     SR_LEVEL_KERNEL = 5,     /* implicit kernel-boundary barrier: launch overhead by
                                 the kernel-fusion method (Eq. 6) */
-    SR_LEVEL_SHUFFLE = 6     /* dependent __shfl_xor_sync chain (Table II "Shuffle") */
+    SR_LEVEL_SHUFFLE = 6,    /* dependent __shfl_xor_sync chain (Table II "Shuffle") */
+    SR_LEVEL_FADD = 7        /* dependent FP32 add chain: the methods' self-check
+                                (Section IX-D; 4 cycles on V100, 6 on P100) */
 } sr_level;
 
 /* Launch configuration.  Zero in any field means "library default". */
@@ -189,6 +191,50 @@ int sr_graph_capture_segmented(const void* x, const int64_t* offsets, int64_t ns
                                const sr_config* cfg, sr_graph* graph);
 int sr_graph_launch(sr_graph graph, sr_stream_t stream);
 int sr_graph_destroy(sr_graph graph);
+
+/* ------------------------------------------------- barrier benchmark */
+
+/* One measurement of a synchronisation level (Section V; methods of Section
+ * IX).  Zero fields take defaults. */
+typedef struct {
+    int level;      /* sr_level */
+    int64_t iters;  /* r1: back-to-back syncs per kernel (default 100000; r2 = r1/10) */
+    int blocks;     /* CTAs (default: 1; cluster size for SR_LEVEL_CLUSTER; SMs for SR_LEVEL_GRID) */
+    int threads;    /* threads per CTA (default: 32 for warp-level levels, 1024 block and
+                       cluster, 256 grid) */
+    int cluster;    /* CTAs per cluster, power of two <= 16 (SR_LEVEL_CLUSTER; default 2) */
+    int group;      /* tile size (power of two) or coalesced-group size, 1..32 (default 32) */
+    int reps;       /* N runs per repeat count for Eqs. 7-8 (default 10) */
+} sr_barrier_config;
+
+typedef struct {
+    double cycles_per_sync;        /* clock64 method (Wong): slowest warp, cycles per sync */
+    double ns_per_sync;            /* Eq. 7: (L(r1) - L(r2)) / (r1 - r2), host clock; for
+                                      SR_LEVEL_KERNEL the launch overhead O of Eq. 6 */
+    double ns_sigma;               /* Eq. 8 (SR_LEVEL_KERNEL: sample s.d. of O) */
+    double syncs_per_cycle_per_sm; /* warp syncs completed per SM per cycle */
+    double clock_mhz;              /* SM clock seen by the run (clock64 / %globaltimer) */
+    double null_kernel_total_ns;   /* SR_LEVEL_KERNEL: null-kernel total latency */
+    int blocks, threads;           /* the shape measured */
+} sr_barrier_result;
+
+/* Measure `level` with `iters` back-to-back syncs and default shape; the
+ * result is kept for sr_barrier_bench_last (per calling thread).  Runs
+ * synchronously on a private stream; allocates and frees its own buffers.
+ * A grid-level shape that cannot be co-resident, or a cluster shape that
+ * cannot be scheduled, returns SR_ERR_LAUNCH without launching (a partial
+ * grid would wait forever: Section VIII-B).
+ * Errors: SR_ERR_ARG (unknown level, iters < 10, bad shape), SR_ERR_LAUNCH,
+ * SR_ERR_CUDA. */
+int sr_barrier_bench(int level, int64_t iters);
+int sr_barrier_bench_ex(const sr_barrier_config* cfg, sr_barrier_result* result);
+int sr_barrier_bench_last(sr_barrier_result* result);
+
+/* Eq. 7 and Eq. 8 on host data: t = (mean(L1) - mean(L2)) / (r1 - r2),
+ * sigma = sqrt(s1^2 + s2^2) / |r1 - r2| (s = sample standard deviation of the
+ * n1, n2 kernel total latencies).  Host only; SR_ERR_ARG if n < 2 or r1 == r2. */
+int sr_differential_latency(const double* L1, int64_t n1, const double* L2, int64_t n2, int64_t r1, int64_t r2,
+                            double* t, double* sigma);
 
 /* ------------------------------------------------- allocation-free sum */
 

@@ -26,7 +26,7 @@ F_BULK = 0x400
 # status codes (sr_status)
 OK, ERR_ARG, ERR_DTYPE, ERR_LAUNCH, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 # barrier levels (sr_level)
-LEVEL_WARP, LEVEL_COALESCED, LEVEL_BLOCK, LEVEL_CLUSTER, LEVEL_GRID, LEVEL_KERNEL, LEVEL_SHUFFLE = range(7)
+LEVEL_WARP, LEVEL_COALESCED, LEVEL_BLOCK, LEVEL_CLUSTER, LEVEL_GRID, LEVEL_KERNEL, LEVEL_SHUFFLE, LEVEL_FADD = range(8)
 
 
 def CLUSTER(log2c: int) -> int:
@@ -42,6 +42,24 @@ class Config(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class BarrierConfig(ctypes.Structure):
+    """Mirror of ``sr_barrier_config``."""
+    _fields_ = [("level", ctypes.c_int), ("iters", ctypes.c_int64), ("blocks", ctypes.c_int),
+                ("threads", ctypes.c_int), ("cluster", ctypes.c_int), ("group", ctypes.c_int),
+                ("reps", ctypes.c_int)]
+
+
+class BarrierResult(ctypes.Structure):
+    """Mirror of ``sr_barrier_result``."""
+    _fields_ = [("cycles_per_sync", ctypes.c_double), ("ns_per_sync", ctypes.c_double),
+                ("ns_sigma", ctypes.c_double), ("syncs_per_cycle_per_sm", ctypes.c_double),
+                ("clock_mhz", ctypes.c_double), ("null_kernel_total_ns", ctypes.c_double),
+                ("blocks", ctypes.c_int), ("threads", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SRError(RuntimeError):
@@ -83,6 +101,15 @@ def load():
     L.sr_graph_launch.argtypes = [vp, vp]
     L.sr_graph_destroy.restype = i32
     L.sr_graph_destroy.argtypes = [vp]
+    L.sr_barrier_bench.restype = i32
+    L.sr_barrier_bench.argtypes = [i32, i64]
+    L.sr_barrier_bench_ex.restype = i32
+    L.sr_barrier_bench_ex.argtypes = [ctypes.POINTER(BarrierConfig), ctypes.POINTER(BarrierResult)]
+    L.sr_barrier_bench_last.restype = i32
+    L.sr_barrier_bench_last.argtypes = [ctypes.POINTER(BarrierResult)]
+    L.sr_differential_latency.restype = i32
+    L.sr_differential_latency.argtypes = [vp, i64, vp, i64, i64, i64, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -243,6 +270,25 @@ class SegmentedGraph:
             self.close()
         except Exception:
             pass
+
+
+def barrier_bench(level: int, iters: int = 0, blocks: int = 0, threads: int = 0, cluster: int = 0,
+                  group: int = 0, reps: int = 0) -> dict:
+    """sr_barrier_bench_ex: one barrier-latency measurement (raises on error)."""
+    c = BarrierConfig(level, iters, blocks, threads, cluster, group, reps)
+    r = BarrierResult()
+    check(lib().sr_barrier_bench_ex(ctypes.byref(c), ctypes.byref(r)), "sr_barrier_bench_ex")
+    return r.as_dict()
+
+
+def differential_latency(L1, L2, r1: int, r2: int):
+    """Eqs. 7-8 computed by the library's host code: returns (t, sigma)."""
+    a = (ctypes.c_double * len(L1))(*L1)
+    b = (ctypes.c_double * len(L2))(*L2)
+    t, sg = ctypes.c_double(), ctypes.c_double()
+    check(lib().sr_differential_latency(a, len(L1), b, len(L2), int(r1), int(r2), ctypes.byref(t),
+                                        ctypes.byref(sg)), "sr_differential_latency")
+    return t.value, sg.value
 
 
 def plan(n: int, dtype: int, config: Config = None) -> Config:

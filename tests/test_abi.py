@@ -100,3 +100,33 @@ def test_segmented_rejects_bad_arguments_without_gpu(lib):
     assert call(block_threads=100) == sr.ERR_ARG
     assert call(grid=100000, block_threads=1024) == sr.ERR_ARG     # more than 65536 warps
     assert call(nseg=0, x=0, off=0, out=0) == sr.OK                 # nothing to do, nothing launched
+
+
+def test_differential_latency_host_code_matches_oracle(lib):
+    """Eqs. 7-8 as computed by the library's host code vs the oracle's."""
+    import numpy as np
+    from oracle import model
+    rng = np.random.default_rng(4)
+    L1 = list(5000 + 3.5 * 1e5 + rng.normal(0, 30, 17))
+    L2 = list(5000 + 3.5 * 1e4 + rng.normal(0, 20, 11))
+    t, sg = sr.differential_latency(L1, L2, 100_000, 10_000)
+    t_o, sg_o = model.differential_latency(L1, L2, 100_000, 10_000)
+    assert t == pytest.approx(t_o, rel=1e-12) and sg == pytest.approx(sg_o, rel=1e-12)
+    c = ctypes.c_double()
+    arr = (ctypes.c_double * 1)(1.0)
+    assert lib.sr_differential_latency(arr, 1, arr, 1, 2, 1, ctypes.byref(c), ctypes.byref(c)) == sr.ERR_ARG
+
+
+def test_barrier_bench_rejects_bad_config_without_gpu(lib):
+    def run(**kw):
+        c = sr.BarrierConfig(**kw)
+        r = sr.BarrierResult()
+        return lib.sr_barrier_bench_ex(ctypes.byref(c), ctypes.byref(r))
+    assert run(level=99) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_WARP, iters=5) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_WARP, group=3) == sr.ERR_ARG          # tiles are powers of two
+    assert run(level=sr.LEVEL_COALESCED, group=33) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_BLOCK, threads=1000) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_CLUSTER, cluster=3) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_GRID, reps=1) == sr.ERR_ARG
+    assert lib.sr_barrier_bench_ex(None, None) == sr.ERR_ARG

@@ -1,0 +1,67 @@
+"""The barrier micro-benchmark runs every level and reports plausible,
+self-consistent numbers (Section V levels; Section IX methods)."""
+import math
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _ok(r):
+    return all(math.isfinite(r[k]) for k in ("cycles_per_sync", "ns_per_sync", "clock_mhz"))
+
+
+@pytest.mark.parametrize("group", [1, 2, 4, 8, 16, 32])
+def test_warp_tile_sync(sr, group):
+    r = sr.barrier_bench(sr.LEVEL_WARP, iters=20000, group=group, reps=3)
+    assert _ok(r) and 0 < r["cycles_per_sync"] < 500
+
+
+@pytest.mark.parametrize("group", [1, 7, 31, 32])
+def test_coalesced_sync(sr, group):
+    r = sr.barrier_bench(sr.LEVEL_COALESCED, iters=20000, group=group, reps=3)
+    assert _ok(r) and 0 < r["cycles_per_sync"] < 2000
+
+
+def test_shuffle_and_block_and_fadd(sr):
+    r = sr.barrier_bench(sr.LEVEL_SHUFFLE, iters=20000, reps=3)
+    assert _ok(r) and 1 < r["cycles_per_sync"] < 200
+    for threads in (32, 256, 1024):
+        r = sr.barrier_bench(sr.LEVEL_BLOCK, iters=20000, threads=threads, reps=3)
+        assert _ok(r) and 0 < r["cycles_per_sync"] < 5000
+    # self-check of the two methods (Section IX-D): the dependent add chain
+    # costs a few cycles per add, and the host-clock differential agrees with
+    # the clock64 count
+    r = sr.barrier_bench(sr.LEVEL_FADD, iters=1_000_000, reps=5)
+    per_add = r["cycles_per_sync"] / 2
+    assert 2 <= per_add <= 12
+    diff_cycles = r["ns_per_sync"] * r["clock_mhz"] / 1e3 / 2
+    assert diff_cycles == pytest.approx(per_add, rel=0.25)
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8, 16])
+def test_cluster_sync(sr, cluster):
+    r = sr.barrier_bench(sr.LEVEL_CLUSTER, iters=20000, cluster=cluster, threads=256, reps=3)
+    assert _ok(r) and 0 < r["cycles_per_sync"] < 20000
+
+
+def test_grid_sync_and_coresidency_guard(sr):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for blocks, threads in ((sms, 32), (sms, 1024), (2 * sms, 256)):
+        r = sr.barrier_bench(sr.LEVEL_GRID, iters=2000, blocks=blocks, threads=threads, reps=3)
+        assert _ok(r) and 100 < r["ns_per_sync"] < 100_000
+        assert r["ns_sigma"] >= 0
+    with pytest.raises(sr.SRError) as e:
+        sr.barrier_bench(sr.LEVEL_GRID, iters=100, blocks=sms * 64, threads=1024, reps=2)
+    assert e.value.status == sr.ERR_LAUNCH
+
+
+def test_kernel_boundary_overhead(sr):
+    r = sr.barrier_bench(sr.LEVEL_KERNEL, reps=5)
+    assert 0 < r["ns_per_sync"] < 100_000
+    assert r["null_kernel_total_ns"] > 0
+    assert sr.lib().sr_barrier_bench(sr.LEVEL_BLOCK, 1000) == sr.OK
+    last = sr.BarrierResult()
+    assert sr.lib().sr_barrier_bench_last(last) == sr.OK
+    assert last.cycles_per_sync > 0
