@@ -217,6 +217,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=N_HEADLINE, help="elements (profiling runs use a smaller case)")
     ap.add_argument("--skip-extras", action="store_true", help="headline loop only (profiling runs)")
+    ap.add_argument("--suite", default=None, choices=["selector", "barrier", "precision", "sweep"],
+                    help="secondary measurement suites (JSON lines); the default run is the headline")
     ap.add_argument("--soak-seconds", type=float, default=0.5,
                     help="untimed back-to-back load before the timed region (clock sampling window)")
     args = ap.parse_args()
@@ -224,6 +226,9 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite:
+        import bench_suites
+        return bench_suites.run(args.suite, args)
 
     import numpy as np
     import torch

@@ -1,0 +1,197 @@
+"""Secondary measurement suites of bench.py (one JSON line per measurement).
+
+  selector  : learned selector vs performance-model selector vs exhaustive
+              autotuning on held-out random shapes (regret), training from
+              ~20,000 autotuner timings
+  barrier   : synchronisation cost per level and shape (Section V / IX)
+  precision : 2^28-element lognormal / cancelling inputs in FP32, BF16 and FP8,
+              plain vs compensated vs compensated + FP64 combine: error against
+              the exact sum and the FP64 oracle, and throughput
+  sweep     : size sweep 2^10..2^30 for FP32 and int32, every grid stage
+"""
+import json
+import math
+import time
+
+import numpy as np
+
+
+def _emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def _time_calls(torch, fn, reps, stream):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def selector_suite(args):
+    import torch
+    import paper_2004_05371_gb300 as sr
+    from paper_2004_05371_gb300 import selector
+    import workloads
+    sr.load()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cands = sr.candidates(sms)
+    t0 = time.time()
+    tr = workloads.selector_shapes(500, seed=101)
+    te = workloads.selector_shapes(1000, seed=202)
+    off_tr = [workloads.shape_offsets(s, i) if s["nseg"] > 1 else None for i, s in enumerate(tr)]
+    off_te = [workloads.shape_offsets(s, 50_000 + i) if s["nseg"] > 1 else None for i, s in enumerate(te)]
+    Ttr = selector.collect_timings(tr, off_tr, cands)
+    Tte = selector.collect_timings(te, off_te, cands)
+    t_collect = time.time() - t0
+    Xtr, Xte = selector.features(tr, off_tr), selector.features(te, off_te)
+    t1 = time.time()
+    sel, losses = selector.train(Xtr, selector.soft_targets(Ttr), steps=4000, lr=3e-3)
+    t_train = time.time() - t1
+    ch = sel.choose(Xte)
+    r_mlp = selector.regret(Tte, ch)
+    r_model = selector.regret(Tte, selector.analytic_choices(te, cands, selector.default_model_params(sms)))
+    # a fixed default: last-block, full grid (8 CTAs/SM), 16-byte vectors
+    fixed = [i for i, c in enumerate(cands) if c.variant == sr.LAST_BLOCK and c.grid == 8 * sms and
+             c.vec_bytes == 16][0]
+    r_fixed = selector.regret(Tte, np.full(len(te), fixed))
+    # inference cost of one shape (the kernel, device time)
+    x1 = torch.from_numpy(((Xte[:1] - sel.mu) / sel.sd).astype(np.float32)).cuda()
+    cls = torch.empty(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    infer_us = _time_calls(torch, lambda: sel.mlp.predict(x1, cls), 200, st) * 1e3
+
+    def summ(r):
+        return {"mean": round(float(r.mean()), 4), "median": round(float(np.median(r)), 4),
+                "p90": round(float(np.quantile(r, 0.9)), 4), "max": round(float(r.max()), 4),
+                "within_5pct": round(float(np.mean(r <= 0.05)), 4)}
+    _emit({"suite": "selector", "train_shapes": len(tr), "train_timings": int(np.isfinite(Ttr).sum()),
+           "heldout_shapes": len(te), "candidates": len(cands), "collect_s": round(t_collect, 1),
+           "train_s": round(t_train, 1), "final_loss": losses[-1][1], "regret_mlp": summ(r_mlp),
+           "regret_model": summ(r_model), "regret_fixed_default": summ(r_fixed),
+           "mlp_inference_us_per_call": round(infer_us, 2)})
+    return 0
+
+
+def barrier_suite(args):
+    import torch
+    import paper_2004_05371_gb300 as sr
+    sr.load()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def run(level, **kw):
+        try:
+            r = sr.barrier_bench(level, **kw)
+            _emit({"suite": "barrier", "level": level, **kw, **{k: (round(v, 3) if isinstance(v, float) else v)
+                                                                for k, v in r.items()}})
+        except sr.SRError as e:
+            _emit({"suite": "barrier", "level": level, **kw, "error": str(e)})
+    for g in (1, 2, 4, 8, 16, 32):
+        run(sr.LEVEL_WARP, group=g)
+    for g in (1, 2, 7, 16, 31, 32):
+        run(sr.LEVEL_COALESCED, group=g)
+    run(sr.LEVEL_SHUFFLE)
+    for t in (32, 64, 128, 256, 512, 1024):
+        run(sr.LEVEL_BLOCK, threads=t)
+    for blocks, t in ((sms, 1024), (2 * sms, 1024), (4 * sms, 512), (8 * sms, 256)):
+        run(sr.LEVEL_BLOCK, blocks=blocks, threads=t, iters=20000)   # throughput with many warps per SM
+    for c in (2, 4, 8, 16):
+        for t in (128, 1024):
+            run(sr.LEVEL_CLUSTER, cluster=c, threads=t, blocks=c)
+    for per_sm in (1, 2, 4, 8):
+        for t in (32, 128, 256, 512, 1024):
+            if per_sm * t <= 2048:
+                run(sr.LEVEL_GRID, blocks=per_sm * sms, threads=t, iters=20000)
+    run(sr.LEVEL_KERNEL, reps=20)
+    run(sr.LEVEL_FADD, iters=1_000_000)
+    return 0
+
+
+def precision_suite(args):
+    import torch
+    import oracle
+    import paper_2004_05371_gb300 as sr
+    import workloads
+    sr.load()
+    n = 1 << 28
+    st = torch.cuda.current_stream()
+    cases = []
+    x = workloads.lognormal_f32(n, seed=0, sigma=4.0)
+    cases.append(("lognormal_s4", "f32", x, None))
+    bits = workloads.to_bf16_bits(x)
+    cases.append(("lognormal_s4", "bf16", bits, None))
+    codes, deq = workloads.to_e4m3_codes(x)
+    cases.append(("lognormal_s4", "fp8", codes, deq))
+    del x
+    for cond in (1e4, 1e5, 1e6, 1e7, 1e8):
+        cases.append(("cancel_%.0e" % cond, "f32", workloads.cancelling_f32(n, cond=cond, seed=0), None))
+    for name, dt, arr, scale in cases:
+        if dt == "f32":
+            exact, s64, sabs = oracle.exact_f32(arr), oracle.sum_f32(arr), oracle.sum_abs_f32(arr)
+            xd = torch.from_numpy(arr).cuda()
+        elif dt == "bf16":
+            exact, s64 = oracle.exact_bf16(arr), oracle.sum_bf16(arr)
+            dec = np.frombuffer((arr.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+            sabs = oracle.sum_abs_f32(dec)
+            xd = torch.from_numpy(arr.view(np.int16)).cuda().view(torch.bfloat16)
+        else:
+            exact, s64 = oracle.exact_e4m3(arr, scale), oracle.sum_e4m3(arr, scale)
+            sabs = oracle.sum_e4m3(arr & 0x7F, scale)
+            xd = torch.from_numpy(arr).cuda()
+        S = oracle.to_float(exact)
+        cond = sabs / abs(S) if S else float("inf")
+        for mode, flags in (("plain", 0), ("kahan", sr.F_KAHAN), ("kahan+fp64", sr.F_KAHAN | sr.F_FP64_COMBINE)):
+            cfg = sr.make_config(sr.LAST_BLOCK | flags, scale=scale or 0.0)
+            out = sr.reduce_sum(xd, config=cfg)
+            got = float(out.item())
+            ms = _time_calls(torch, lambda: sr.reduce_sum(xd, config=cfg, out=out), 10, st)
+            _emit({"suite": "precision", "input": name, "dtype": dt, "mode": mode, "n": n,
+                   "cond": cond, "exact": S, "fp64_oracle": s64, "gpu": got,
+                   "abs_err": abs(got - S), "rel_err": abs(got - S) / abs(S) if S else None,
+                   "err_vs_fp64_oracle": abs(got - s64), "fp64_oracle_err": abs(s64 - S),
+                   "gate_plain_4eps_sumabs": 4 * 2.0 ** -23 * sabs,
+                   "gate_kahan_abs": (2 * 2.0 ** -24 + n * 2.0 ** -48) * sabs,
+                   "gbs": round(xd.numel() * xd.element_size() / (ms * 1e-3) / 1e9, 1)})
+        del xd
+        torch.cuda.empty_cache()
+    return 0
+
+
+def sweep_suite(args):
+    import torch
+    import paper_2004_05371_gb300 as sr
+    sr.load()
+    st = torch.cuda.current_stream()
+    big = torch.empty(1 << 30, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+    bigi = big.view(torch.int32)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for dt, src in (("f32", big), ("i32", bigi)):
+        for k in range(10, 31, 2):
+            n = 1 << k
+            x = src[:n]
+            for name, v in (("auto", sr.AUTO), ("two_kernel", sr.TWO_KERNEL), ("atomic", sr.ATOMIC),
+                            ("last_block", sr.LAST_BLOCK), ("grid_sync", sr.GRID_SYNC),
+                            ("single_cluster_16", sr.SINGLE_CLUSTER | sr.CLUSTER(4)),
+                            ("last_block_cluster4", sr.LAST_BLOCK | sr.CLUSTER(2)),
+                            ("last_block_bulk", sr.LAST_BLOCK | sr.F_BULK)):
+                cfg = sr.make_config(v)
+                out = sr.reduce_sum(x, config=cfg)
+                warm = _time_calls(torch, lambda: sr.reduce_sum(x, config=cfg, out=out), 20, st)
+                # cold: overwrite L2 between calls (the flush write is timed separately and subtracted)
+                fl = _time_calls(torch, lambda: flush.fill_(1), 5, st)
+                both = _time_calls(torch, lambda: (flush.fill_(1), sr.reduce_sum(x, config=cfg, out=out)), 5, st)
+                cold = max(both - fl, 1e-6)
+                _emit({"suite": "sweep", "dtype": dt, "log2n": k, "variant": name,
+                       "warm_us": round(warm * 1e3, 2), "cold_us": round(cold * 1e3, 2),
+                       "warm_gbs": round(n * 4 / (warm * 1e-3) / 1e9, 1),
+                       "cold_gbs": round(n * 4 / (cold * 1e-3) / 1e9, 1)})
+    return 0
+
+
+def run(name, args):
+    return {"selector": selector_suite, "barrier": barrier_suite, "precision": precision_suite,
+            "sweep": sweep_suite}[name](args)

@@ -236,6 +236,89 @@ int sr_barrier_bench_last(sr_barrier_result* result);
 int sr_differential_latency(const double* L1, int64_t n1, const double* L2, int64_t n2, int64_t r1, int64_t r2,
                             double* t, double* sigma);
 
+/* ---------------------------------------------- autotuner and selection */
+
+/* The candidate launch configurations: grid stage {SR_TWO_KERNEL, SR_ATOMIC,
+ * SR_LAST_BLOCK, SR_GRID_SYNC} x grid {8 CTAs, 1, 2, 4, 8 CTAs per SM} of 256
+ * threads x vector width {16, 32} bytes = 40 (unroll 4); with `full`, also x
+ * unroll {1, 2, 4, 8} = 160.  `sms` is the device's SM count.  With out ==
+ * NULL returns the count; else fills out[0..count) (cap entries available)
+ * and returns the count.  Negative return = -sr_status.  Host only. */
+int sr_candidates(int full, int sms, sr_config* out, int cap);
+
+/* Exhaustive autotuning: times every candidate on the caller's data with
+ * CUDA events on `stream` (one untimed warm-up call, then `reps` calls back
+ * to back) and writes the mean microseconds per call to us[i]; a candidate
+ * that cannot run (SR_ERR_LAUNCH / SR_ERR_UNSUPPORTED / SR_ERR_ARG) gets
+ * +infinity.  offsets == NULL: single array of n elements (sr_reduce_sum_ex);
+ * else segmented over nseg segments (sr_reduce_sum_segmented_ex, n unused).
+ * out receives the last result.  Synchronises `stream`.
+ * Errors: SR_ERR_ARG (bad arrays / reps), or the first CUDA error. */
+int sr_autotune(const void* x, int64_t n, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                const sr_config* cands, int ncand, int reps, float* us, sr_stream_t stream);
+
+/* Parameters of the performance model (Section VII-A) for one GPU. */
+typedef struct {
+    int sms;
+    double hbm_bytes_per_ns;  /* device-memory throughput at saturation (GB/s) */
+    double mem_latency_ns;    /* T: latency of a device-memory access (Little's law) */
+    double launch_ns;         /* implicit kernel-boundary barrier (Eq. 6 overhead) */
+    double grid_sync_ns;      /* one grid.sync() */
+    double last_block_ns;     /* fence + ticket + final reduction of the last unit */
+    double atomic_ns;         /* one global atomic finish */
+    double per_cta_ns;        /* partial-result cost per CTA per SM */
+    double per_segment_ns;    /* per-segment cost of the segmented kernel, per warp */
+} sr_model_params;
+
+/* The model evaluated over candidate configurations: for each candidate,
+ * throughput Thr = min(peak, bytes in flight / T) (Eq. 1 read as the
+ * concurrency a launch shape sustains), C = T * Thr, and predicted time
+ * launch + T + T_sync(stage) + max(0, N - C) / Thr (Eqs. 2-3) plus the
+ * per-CTA and per-segment terms; N = n * sizeof(dtype).  Writes the
+ * predictions (microseconds) to predicted_us when non-NULL and returns the
+ * index of the cheapest candidate (or -sr_status).  Host only. */
+int sr_select_analytic(const sr_model_params* params, int64_t n, int dtype, int64_t nseg, const sr_config* cands,
+                       int ncand, float* predicted_us);
+
+/* Feature vector of one call for the learned selector (host only): 9 floats
+ * = log2 n, one-hot dtype (4), log2 nseg, log2(1 + mean), log2(1 + std),
+ * log2(1 + max) of the segment lengths (a single array: nseg = 1, mean = max
+ * = n, std = 0).  SR_ERR_ARG on negative sizes, nseg < 1 or a bad dtype. */
+#define SR_SELECTOR_FEATURES 9
+int sr_selector_features(int64_t n, int dtype, int64_t nseg, double len_mean, double len_std, double len_max,
+                         float* out);
+
+/* ----------------------------------------------------- learned selector */
+
+/* A small MLP cost model that picks a candidate configuration per call (no
+ * counterpart in the paper): in_dim features -> hidden (ReLU) -> hidden (ReLU)
+ * -> out_dim logits, trained on autotuner timings with a softmax
+ * cross-entropy against soft target distributions, by this library's own
+ * forward / backward / Adam kernels.  Parameters and Adam state live on the
+ * device.  Limits: in_dim <= 32, hidden <= 64, 2 <= out_dim <= 64.
+ * Parameter layout (one float array, row-major): W1[in][hidden], b1[hidden],
+ * W2[hidden][hidden], b2[hidden], W3[hidden][out], b3[out]. */
+typedef struct sr_mlp_s* sr_mlp;
+int sr_mlp_create(int in_dim, int hidden, int out_dim, sr_mlp* mlp);   /* parameters start at 0 */
+int sr_mlp_destroy(sr_mlp mlp);
+int64_t sr_mlp_param_count(sr_mlp mlp);
+/* Host copies of the parameters (count must equal sr_mlp_param_count);
+ * set also resets the Adam state.  Synchronous. */
+int sr_mlp_set_params(sr_mlp mlp, const float* host_params, int64_t count);
+int sr_mlp_get_params(sr_mlp mlp, float* host_params, int64_t count);
+/* One training step on a device batch: X [batch][in_dim], Q [batch][out_dim]
+ * (each row a probability distribution).  Computes the mean cross-entropy
+ * -1/B sum_b sum_o Q log softmax(z) and its gradient; writes the loss to
+ * *loss (device float, optional) and the gradient to grad (device, param_count
+ * floats, optional), then applies one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8) with learning rate lr — none when lr == 0.  The per-CTA gradient
+ * partials are summed in a fixed order: results are deterministic. */
+int sr_mlp_train_step(sr_mlp mlp, const float* X, const float* Q, int batch, float lr, float* loss, float* grad,
+                      sr_stream_t stream);
+/* Inference kernel: cls[b] = argmax_o logits (lowest index on ties) for a
+ * device batch X [batch][in_dim]; logits (device, optional) receives z. */
+int sr_mlp_predict(sr_mlp mlp, const float* X, int batch, int* cls, float* logits, sr_stream_t stream);
+
 /* ------------------------------------------------- allocation-free sum */
 
 /* The last-block-done sum (SR_LAST_BLOCK, LDG load path) for callers that must

@@ -62,6 +62,14 @@ class BarrierResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ModelParams(ctypes.Structure):
+    """Mirror of ``sr_model_params``."""
+    _fields_ = [("sms", ctypes.c_int), ("hbm_bytes_per_ns", ctypes.c_double), ("mem_latency_ns", ctypes.c_double),
+                ("launch_ns", ctypes.c_double), ("grid_sync_ns", ctypes.c_double),
+                ("last_block_ns", ctypes.c_double), ("atomic_ns", ctypes.c_double), ("per_cta_ns", ctypes.c_double),
+                ("per_segment_ns", ctypes.c_double)]
+
+
 class SRError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -110,6 +118,31 @@ def load():
     L.sr_differential_latency.restype = i32
     L.sr_differential_latency.argtypes = [vp, i64, vp, i64, i64, i64, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
+    L.sr_candidates.restype = i32
+    L.sr_candidates.argtypes = [i32, i32, ctypes.POINTER(Config), i32]
+    L.sr_autotune.restype = i32
+    L.sr_autotune.argtypes = [vp, i64, vp, i64, i32, vp, ctypes.POINTER(Config), i32, i32,
+                              ctypes.POINTER(ctypes.c_float), vp]
+    L.sr_select_analytic.restype = i32
+    L.sr_select_analytic.argtypes = [ctypes.POINTER(ModelParams), i64, i32, i64, ctypes.POINTER(Config), i32,
+                                     ctypes.POINTER(ctypes.c_float)]
+    L.sr_mlp_create.restype = i32
+    L.sr_mlp_create.argtypes = [i32, i32, i32, ctypes.POINTER(vp)]
+    L.sr_mlp_destroy.restype = i32
+    L.sr_mlp_destroy.argtypes = [vp]
+    L.sr_mlp_param_count.restype = i64
+    L.sr_mlp_param_count.argtypes = [vp]
+    L.sr_mlp_set_params.restype = i32
+    L.sr_mlp_set_params.argtypes = [vp, vp, i64]
+    L.sr_mlp_get_params.restype = i32
+    L.sr_mlp_get_params.argtypes = [vp, vp, i64]
+    L.sr_mlp_train_step.restype = i32
+    L.sr_mlp_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.sr_mlp_predict.restype = i32
+    L.sr_mlp_predict.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.sr_selector_features.restype = i32
+    L.sr_selector_features.argtypes = [i64, i32, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_float)]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -289,6 +322,91 @@ def differential_latency(L1, L2, r1: int, r2: int):
     check(lib().sr_differential_latency(a, len(L1), b, len(L2), int(r1), int(r2), ctypes.byref(t),
                                         ctypes.byref(sg)), "sr_differential_latency")
     return t.value, sg.value
+
+
+def candidates(sms: int, full: bool = False):
+    """The candidate configurations (sr_candidates) as a ctypes array."""
+    cnt = lib().sr_candidates(int(full), int(sms), None, 0)
+    if cnt < 0:
+        raise SRError(-cnt, "sr_candidates")
+    arr = (Config * cnt)()
+    got = lib().sr_candidates(int(full), int(sms), arr, cnt)
+    if got != cnt:
+        raise SRError(-got if got < 0 else ERR_ARG, "sr_candidates")
+    return arr
+
+
+def autotune(x_ptr: int, n: int, dtype: int, out_ptr: int, cands, reps: int = 5, offsets_ptr: int = 0,
+             nseg: int = 0, stream=None):
+    """sr_autotune: microseconds per call for every candidate (inf = cannot run)."""
+    us = (ctypes.c_float * len(cands))()
+    check(lib().sr_autotune(ctypes.c_void_p(x_ptr), int(n), ctypes.c_void_p(offsets_ptr or None), int(nseg),
+                            int(dtype), ctypes.c_void_p(out_ptr), cands, len(cands), int(reps), us,
+                            ctypes.c_void_p(_stream(stream))), "sr_autotune")
+    return list(us)
+
+
+def select_analytic(params: ModelParams, n: int, dtype: int, nseg: int, cands):
+    """sr_select_analytic: (index of the predicted-fastest candidate, predictions in us)."""
+    pred = (ctypes.c_float * len(cands))()
+    i = lib().sr_select_analytic(ctypes.byref(params), int(n), int(dtype), int(nseg), cands, len(cands), pred)
+    if i < 0:
+        raise SRError(-i, "sr_select_analytic")
+    return i, list(pred)
+
+
+class MLP:
+    """Handle of an sr_mlp (device-resident parameters).  Argument marshalling
+    only: training and inference run in the library's kernels."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int):
+        self.h = ctypes.c_void_p()
+        check(lib().sr_mlp_create(in_dim, hidden, out_dim, ctypes.byref(self.h)), "sr_mlp_create")
+        self.dims = (in_dim, hidden, out_dim)
+        self.P = int(lib().sr_mlp_param_count(self.h))
+
+    def set_params(self, host_array):
+        import numpy as np
+        a = np.ascontiguousarray(host_array, dtype=np.float32)
+        check(lib().sr_mlp_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size), "sr_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.P, np.float32)
+        check(lib().sr_mlp_get_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size), "sr_mlp_get_params")
+        return a
+
+    def train_step(self, X, Q, lr: float, loss=None, grad=None, stream=None):
+        """X, Q: CUDA float32 tensors [B, in] / [B, out]; loss: CUDA float32
+        scalar tensor (optional); grad: CUDA float32 [P] (optional)."""
+        B = X.shape[0]
+        check(lib().sr_mlp_train_step(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Q.data_ptr()), B,
+                                      float(lr), ctypes.c_void_p(loss.data_ptr() if loss is not None else None),
+                                      ctypes.c_void_p(grad.data_ptr() if grad is not None else None),
+                                      ctypes.c_void_p(_stream(stream))), "sr_mlp_train_step")
+
+    def predict(self, X, cls, logits=None, stream=None):
+        check(lib().sr_mlp_predict(self.h, ctypes.c_void_p(X.data_ptr()), X.shape[0], ctypes.c_void_p(cls.data_ptr()),
+                                   ctypes.c_void_p(logits.data_ptr() if logits is not None else None),
+                                   ctypes.c_void_p(_stream(stream))), "sr_mlp_predict")
+
+    def close(self):
+        if self.h:
+            lib().sr_mlp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def selector_features(n: int, dtype: int, nseg: int, len_mean: float, len_std: float, len_max: float):
+    out = (ctypes.c_float * 9)()
+    check(lib().sr_selector_features(int(n), int(dtype), int(nseg), float(len_mean), float(len_std),
+                                     float(len_max), out), "sr_selector_features")
+    return list(out)
 
 
 def plan(n: int, dtype: int, config: Config = None) -> Config:

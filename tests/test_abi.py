@@ -130,3 +130,36 @@ def test_barrier_bench_rejects_bad_config_without_gpu(lib):
     assert run(level=sr.LEVEL_CLUSTER, cluster=3) == sr.ERR_ARG
     assert run(level=sr.LEVEL_GRID, reps=1) == sr.ERR_ARG
     assert lib.sr_barrier_bench_ex(None, None) == sr.ERR_ARG
+
+
+def test_candidate_set(lib):
+    c40 = sr.candidates(152)
+    assert len(c40) == 40
+    c160 = sr.candidates(152, full=True)
+    assert len(c160) == 160
+    stages = {c.variant for c in c40}
+    assert stages == {sr.TWO_KERNEL, sr.ATOMIC, sr.LAST_BLOCK, sr.GRID_SYNC}
+    assert {c.grid for c in c40} == {8, 152, 304, 608, 1216}
+    assert {c.vec_bytes for c in c40} == {16, 32} and {c.unroll for c in c160} == {1, 2, 4, 8}
+    assert lib.sr_candidates(0, 0, None, 0) < 0
+
+
+def test_analytic_selector_is_eq2(lib):
+    """Two candidates that differ only in grid size: with the per-CTA cost as
+    the extra synchronisation of the larger grid, the host selector's choice
+    must equal Eq. 2 of the oracle's performance model for every N."""
+    import numpy as np
+    from oracle import model
+    p = sr.ModelParams(sms=100, hbm_bytes_per_ns=5000.0, mem_latency_ns=800.0, launch_ns=0.0, grid_sync_ns=0.0,
+                       last_block_ns=0.0, atomic_ns=0.0, per_cta_ns=3000.0, per_segment_ns=0.0)
+    basic = sr.make_config(sr.LAST_BLOCK, grid=8, block_threads=256, vec_bytes=16, unroll=4)
+    more = sr.make_config(sr.LAST_BLOCK, grid=800, block_threads=256, vec_bytes=16, unroll=4)
+    cands = (sr.Config * 2)(basic, more)
+    warp_bytes = 32 * 16 * 4
+    thr_b = min(p.hbm_bytes_per_ns, 8 * 8 * warp_bytes / p.mem_latency_ns)
+    thr_m = min(p.hbm_bytes_per_ns, 800 * 8 * warp_bytes / p.mem_latency_ns)
+    t_sync = p.per_cta_ns * (800 - 8) / p.sms
+    for N in np.geomspace(1e3, 1e9, 600):
+        n = int(N) // 4
+        i, _ = sr.select_analytic(p, n, sr.F32, 1, cands)
+        assert (i == 0) == model.prefer_basic(n * 4, p.mem_latency_ns, t_sync, thr_b, thr_m), N

@@ -1,0 +1,116 @@
+"""The selector's MLP kernels against the FP64 oracle (oracle/mlp.py):
+forward logits, loss, gradient, one Adam step, argmax inference, determinism;
+then the learned selector against the exhaustive autotuner and the
+performance-model selector on held-out shapes."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+import workloads
+
+pytestmark = pytest.mark.gpu
+DIMS = (9, 64, 40)
+
+
+def _setup(seed=0, B=37):
+    rng = np.random.default_rng(seed)
+    P = omlp.param_count(DIMS)
+    p = rng.normal(0, 0.3, P).astype(np.float32)
+    X = rng.normal(0, 1, (B, DIMS[0])).astype(np.float32)
+    Q = rng.dirichlet(np.ones(DIMS[2]) * 0.3, size=B).astype(np.float32)
+    return p, X, Q
+
+
+def test_gradient_and_loss_vs_fp64_oracle(sr):
+    for B in (1, 16, 37, 300):
+        p, X, Q = _setup(B, B)
+        m = sr.MLP(*DIMS)
+        m.set_params(p)
+        loss = torch.zeros((), dtype=torch.float32, device="cuda")
+        grad = torch.zeros(m.P, dtype=torch.float32, device="cuda")
+        m.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda(), 0.0, loss=loss, grad=grad)
+        torch.cuda.synchronize()
+        g = grad.cpu().numpy().astype(np.float64)
+        g_ref = omlp.grad(p, X, Q, DIMS)
+        assert np.max(np.abs(g - g_ref)) <= 2e-4 * np.max(np.abs(g_ref)) + 1e-7, B
+        assert float(loss.item()) == pytest.approx(omlp.loss(p, X, Q, DIMS), rel=2e-5)
+        assert np.array_equal(m.get_params(), p)      # lr == 0: no update
+        m.close()
+
+
+def test_adam_step_vs_oracle(sr):
+    p, X, Q = _setup(3, 64)
+    m = sr.MLP(*DIMS)
+    m.set_params(p)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    pr, mm, vv = p.astype(np.float64), np.zeros(p.size), np.zeros(p.size)
+    for t in range(1, 4):
+        g_ref = omlp.grad(pr, X, Q, DIMS)
+        pr, mm, vv = omlp.adam_step(pr, mm, vv, g_ref, t, lr=1e-3)
+        m.train_step(Xd, Qd, 1e-3)
+    got = m.get_params().astype(np.float64)
+    assert np.max(np.abs(got - pr)) <= 5e-6 + 1e-4 * np.max(np.abs(pr))
+    m.close()
+
+
+def test_predict_and_determinism(sr):
+    p, X, Q = _setup(5, 200)
+    m = sr.MLP(*DIMS)
+    m.set_params(p)
+    Xd = torch.from_numpy(X).cuda()
+    cls = torch.empty(200, dtype=torch.int32, device="cuda")
+    logits = torch.empty(200, DIMS[2], dtype=torch.float32, device="cuda")
+    m.predict(Xd, cls, logits)
+    torch.cuda.synchronize()
+    _, _, z = omlp.forward(p, X, DIMS)
+    assert np.max(np.abs(logits.cpu().numpy() - z)) <= 1e-4 * np.max(np.abs(z))
+    top2 = np.sort(z, axis=1)[:, -2:]
+    clear = (top2[:, 1] - top2[:, 0]) > 1e-3
+    assert np.array_equal(cls.cpu().numpy()[clear], np.argmax(z, axis=1)[clear])
+    Qd = torch.from_numpy(Q).cuda()
+    g1 = torch.zeros(m.P, device="cuda")
+    g2 = torch.zeros(m.P, device="cuda")
+    m.train_step(Xd, Qd, 0.0, grad=g1)
+    m.train_step(Xd, Qd, 0.0, grad=g2)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    m.close()
+
+
+def test_training_learns_a_separable_task(sr):
+    from paper_2004_05371_gb300 import selector
+    rng = np.random.default_rng(7)
+    W = rng.normal(size=(9, 40))
+    X = rng.normal(size=(4000, 9)).astype(np.float32)
+    labels = np.argmax(X @ W, axis=1)
+    Q = np.eye(40, dtype=np.float32)[labels]
+    sel, losses = selector.train(X[:3000], Q[:3000], steps=1500, lr=3e-3, seed=1)
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    acc = np.mean(sel.choose(X[3000:]) == labels[3000:])
+    assert acc > 0.8, acc
+
+
+@pytest.mark.slow
+def test_learned_selector_beats_the_model_without_it(sr):
+    """Train on autotuner timings of random shapes, evaluate on held-out
+    shapes: the MLP's mean regret against exhaustive autotuning is reported
+    next to the performance-model selector's; the MLP must do better."""
+    from paper_2004_05371_gb300 import selector
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cands = sr.candidates(sms)
+    tr = workloads.selector_shapes(160, seed=11)
+    te = workloads.selector_shapes(120, seed=12)
+    for s in tr + te:                     # keep the test quick: n <= 2^26
+        s["n"] = min(s["n"], 1 << 26)
+        s["nseg"] = min(s["nseg"], s["n"])
+    off_tr = [workloads.shape_offsets(s, i) if s["nseg"] > 1 else None for i, s in enumerate(tr)]
+    off_te = [workloads.shape_offsets(s, 10_000 + i) if s["nseg"] > 1 else None for i, s in enumerate(te)]
+    Ttr = selector.collect_timings(tr, off_tr, cands)
+    Tte = selector.collect_timings(te, off_te, cands)
+    sel, _ = selector.train(selector.features(tr, off_tr), selector.soft_targets(Ttr), steps=1500)
+    r_mlp = selector.regret(Tte, sel.choose(selector.features(te, off_te)))
+    r_model = selector.regret(Tte, selector.analytic_choices(te, cands, selector.default_model_params(sms)))
+    print("mean regret: mlp %.4f  model %.4f" % (r_mlp.mean(), r_model.mean()))
+    assert np.all(np.isfinite(r_mlp))
+    assert r_mlp.mean() < r_model.mean()

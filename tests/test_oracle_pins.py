@@ -262,3 +262,46 @@ def test_gamma_and_stated_bound():
         acc = np.float32(acc + v)
     err = abs(Fraction(float(acc)) - oracle.exact_f32(x))
     assert err <= Fraction(oracle.fp32_tree_bound(float(np.sum(np.abs(x), dtype=np.float64)), x.size - 1))
+
+
+# ------------------------------------------------------------- MLP oracle
+def test_mlp_oracle_closed_forms():
+    from oracle import mlp
+    dims = (3, 5, 4)
+    zero = np.zeros(mlp.param_count(dims))
+    X = np.random.default_rng(0).normal(size=(7, 3))
+    Q = np.eye(4)[[0, 1, 2, 3, 0, 1, 2]]
+    # all-zero network: uniform softmax, loss log K, d/db3 = mean(1/K - q)
+    assert mlp.loss(zero, X, Q, dims) == pytest.approx(math.log(4))
+    g = mlp.grad(zero, X, Q, dims)
+    assert np.allclose(g[-4:], (0.25 - Q).mean(axis=0))
+    assert np.allclose(g[:-4], 0.0)
+    # 1-1-2 network by hand: z = (ab c, ab d) for x = 1, a, b > 0
+    a, b, c, d = 0.7, 1.3, 0.4, -0.9
+    p = np.array([a, 0.0, b, 0.0, c, d, 0.0, 0.0])
+    z0, z1 = a * b * c, a * b * d
+    assert mlp.loss(p, [[1.0]], [[1.0, 0.0]], (1, 1, 2)) == pytest.approx(math.log1p(math.exp(z1 - z0)))
+
+
+def test_mlp_oracle_gradient_vs_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(1)
+    dims = (6, 8, 5)
+    p = rng.normal(scale=0.5, size=mlp.param_count(dims))
+    X = rng.normal(size=(9, 6))
+    Q = rng.dirichlet(np.ones(5), size=9)
+    g = mlp.grad(p, X, Q, dims)
+    h = 1e-6
+    for k in range(p.size):
+        e = np.zeros_like(p)
+        e[k] = h
+        fd = (mlp.loss(p + e, X, Q, dims) - mlp.loss(p - e, X, Q, dims)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), k
+
+
+def test_mlp_oracle_adam_first_step_is_sign_step():
+    from oracle import mlp
+    g = np.array([0.3, -2.0, 1e-3])
+    p1, m, v = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
+    # bias-corrected first step: mhat = g, vhat = g^2, so the step is lr * sign(g)
+    assert np.allclose(p1, -0.01 * np.sign(g), rtol=1e-4)

@@ -21,6 +21,11 @@ Recipes (numpy ``default_rng(seed)``, PCG64):
                    rest cancel exactly (binary32 cannot carry a smaller
                    relative perturbation).  The achieved cond is measured by
                    the oracle, not assumed.
+  selector_shapes  random call shapes for the selector: log2 n ~ U[10, 30],
+                   dtype uniform over {f32, i32, bf16, fp8}, nseg log-uniform
+                   in [1, 1e5] (at most n), segment-length sigma ~ U[0.5, 2.5].
+  shape_offsets    CSR offsets of one such shape: lognormal(0, sigma) weights
+                   scaled to total n (rounded; the remainder goes to the last).
   segment_offsets  CSR offsets of nseg segments whose lengths are
                    round(lognormal(ln median, sigma)) clipped to [lo, hi],
                    then scaled proportionally (and re-clipped) so that the
@@ -116,5 +121,27 @@ def random_segment_offsets(nseg: int, max_len: int, seed: int = 0,
     lens = rng.integers(0, max_len, int(nseg), endpoint=True)
     lens[rng.random(int(nseg)) < p_empty] = 0
     off = np.zeros(int(nseg) + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    return off
+
+
+def selector_shapes(count: int, seed: int):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(int(count)):
+        n = int(2 ** rng.uniform(10, 30))
+        nseg = int(min(n, round(10 ** rng.uniform(0, 5))))
+        out.append({"n": n, "dtype": int(rng.integers(0, 4)), "nseg": max(1, nseg),
+                    "sigma": float(rng.uniform(0.5, 2.5))})
+    return out
+
+
+def shape_offsets(shape, seed: int) -> np.ndarray:
+    n, nseg = shape["n"], shape["nseg"]
+    rng = np.random.default_rng(seed)
+    w = rng.lognormal(0.0, shape["sigma"], nseg)
+    lens = np.floor(w / w.sum() * n).astype(np.int64)
+    lens[-1] += n - int(lens.sum())
+    off = np.zeros(nseg + 1, dtype=np.int64)
     np.cumsum(lens, out=off[1:])
     return off
