@@ -50,10 +50,13 @@ __device__ __forceinline__ void lb_round(const int64_t* off, int64_t key, int la
         if (k > 0) lo = lo + (int64_t)(k - 1) * step + 1;
     }
 }
+// hi - lo <= 32 here.  With exactly 32 candidates left, every lane may hold
+// an offset below the key: the ballot is then empty and the answer is hi.
 __device__ __forceinline__ int64_t lb_final(const int64_t* off, int64_t key, int lane, int64_t lo, int64_t hi) {
     const int64_t i = lo + lane;
     const bool pred = (i < hi) ? (__ldg(off + i) >= key) : true;
     const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (m == 0) return hi;
     const int64_t r = lo + (__ffs(m) - 1);
     return r < hi ? r : hi;
 }

@@ -170,3 +170,28 @@ def test_full_size_lognormal_10k_segments(sr):
     for st in STAGES:
         got = sr.reduce_sum_segmented(xd, od, variant=st).cpu().numpy().astype(np.float64)
         assert np.all(np.abs(got - ex) <= tol), st
+
+
+@pytest.mark.parametrize("nseg", [32, 64, 1024, 1056, 32 * 33])
+def test_search_with_exactly_32_candidates_left(sr, nseg):
+    """Layouts where a warp's segment search ends with exactly 32 candidates
+    that all start before its piece: nseg - 1 one-element segments, then one
+    long segment covering every later warp."""
+    n_long = 1 << 20
+    lens = np.ones(nseg, np.int64)
+    lens[-1] = n_long
+    off = np.zeros(nseg + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    x = workloads.uniform_i32(int(off[-1]), seed=nseg)
+    xf = workloads.uniform_f32(int(off[-1]), seed=nseg)
+    for st in STAGES:
+        for grid in (0, 4, 64):
+            _check(sr, x, off, st, grid=grid)
+            _check(sr, xf, off, st, grid=grid)
+    rng = np.random.default_rng(nseg)
+    off2 = np.zeros(nseg + 1, np.int64)
+    np.cumsum(rng.integers(0, 3, nseg) * (rng.random(nseg) < 0.97) + (rng.random(nseg) < 0.03) * 50_000,
+              out=off2[1:])
+    x2 = workloads.uniform_i32(int(off2[-1]) + 1, seed=1)
+    for st in STAGES:
+        _check(sr, x2, off2, st)
