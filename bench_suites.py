@@ -8,6 +8,7 @@
               plain vs compensated vs compensated + FP64 combine: error against
               the exact sum and the FP64 oracle, and throughput
   sweep     : size sweep 2^10..2^30 for FP32 and int32, every grid stage
+  segmented : the batched segmented workload in one graph launch per step
 """
 import json
 import math
@@ -192,6 +193,35 @@ def sweep_suite(args):
     return 0
 
 
+def segmented_suite(args):
+    """The batched workload alone: 10,000 lognormal segments (median 4096,
+    sigma 1.94, clipped to [1, 2^24]) totalling about args.n FP32 elements,
+    in one library-owned graph launch per step (also the ncu capture target)."""
+    import torch
+    import paper_2004_05371_gb300 as sr
+    import workloads
+    sr.load()
+    nseg = 10_000
+    off = workloads.segment_offsets(nseg, args.n, seed=0)
+    n = int(off[-1])
+    x = torch.from_numpy(workloads.uniform_f32(n, seed=0)).cuda()
+    od = torch.from_numpy(off).cuda()
+    out = torch.empty(nseg, dtype=torch.float32, device="cuda")
+    cfg = sr.make_config(args.variant if args.variant is not None else sr.AUTO)
+    sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(), cfg))
+    g = sr.SegmentedGraph(x, od, out, cfg)
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        g.launch(st)
+    ms = _time_calls(torch, lambda: g.launch(st), args.steps, st)
+    r = sr.plan_segmented(nseg, sr.F32, cfg)
+    _emit({"suite": "segmented", "n": n, "nseg": nseg, "us_per_launch": round(ms * 1e3, 2),
+           "gbs": round(n * 4 / (ms * 1e-3) / 1e9, 1), "stage": r.variant & sr.STAGE_MASK, "grid": r.grid,
+           "block": r.block_threads, "vec_bytes": r.vec_bytes, "unroll": r.unroll})
+    g.close()
+    return 0
+
+
 def run(name, args):
     return {"selector": selector_suite, "barrier": barrier_suite, "precision": precision_suite,
-            "sweep": sweep_suite}[name](args)
+            "sweep": sweep_suite, "segmented": segmented_suite}[name](args)

@@ -137,6 +137,20 @@ typedef struct {
 int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant,
                   sr_stream_t stream);
 
+/* End-to-end form: x and out are HOST pointers (x preferably page-locked, e.g.
+ * cudaHostAlloc / cudaHostRegister, so copies run asynchronously).  The input
+ * is copied to the device in 64 MiB chunks through two library-owned staging
+ * buffers on two copy streams, each chunk reduced on `stream` while the next
+ * one is copied (the chunk units' partials go to disjoint workspace slots),
+ * one final kernel combines all partials in order, and the result is copied
+ * back to *out.  Blocks until the result is in *out.  cfg: NULL, or stage
+ * SR_AUTO / SR_TWO_KERNEL with optional SR_F_KAHAN / SR_F_FP64_COMBINE and
+ * launch-shape fields; other stages or SR_F_BULK -> SR_ERR_UNSUPPORTED.
+ * The first call on a stream allocates the staging buffers (128 MiB).
+ * Errors: as sr_reduce_sum_ex. */
+int sr_reduce_sum_host(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg,
+                       sr_stream_t stream);
+
 /* Same with an explicit launch configuration (NULL cfg = defaults). */
 int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out,
                      const sr_config* cfg, sr_stream_t stream);

@@ -143,6 +143,8 @@ def load():
     L.sr_selector_features.restype = i32
     L.sr_selector_features.argtypes = [i64, i32, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_float)]
+    L.sr_reduce_sum_host.restype = i32
+    L.sr_reduce_sum_host.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -220,6 +222,13 @@ def reduce_sum_noalloc_ptr(x_ptr: int, n: int, dtype: int, out_ptr: int, config:
     cfg = ctypes.byref(config) if config is not None else None
     return lib().sr_reduce_sum_noalloc(ctypes.c_void_p(x_ptr), int(n), int(dtype), ctypes.c_void_p(out_ptr), cfg,
                                        ctypes.c_void_p(_stream(stream)))
+
+
+def reduce_sum_host_ptr(x_ptr: int, n: int, dtype: int, out_ptr: int, config: Config = None, stream=None) -> int:
+    """Raw call of sr_reduce_sum_host (HOST input and output pointers)."""
+    cfg = ctypes.byref(config) if config is not None else None
+    return lib().sr_reduce_sum_host(ctypes.c_void_p(x_ptr), int(n), int(dtype), ctypes.c_void_p(out_ptr), cfg,
+                                    ctypes.c_void_p(_stream(stream)))
 
 
 def reduce_sum(x, variant: int = AUTO, out=None, config: Config = None, stream=None, **cfg_fields):

@@ -159,8 +159,25 @@ template <class A> __device__ __forceinline__ void acc_word_fp8(A& a, uint32_t w
     acc_add_f(a, f1.x);
     acc_add_f(a, f1.y);
 }
-template <> __device__ __forceinline__ void acc_word<kDtFP8, float>(float& a, uint32_t w) { acc_word_fp8(a, w); }
-template <> __device__ __forceinline__ void acc_word<kDtFP8, Pair>(Pair& a, uint32_t w) { acc_word_fp8(a, w); }
+template <> __device__ __forceinline__ void acc_word<kDtFP8, float>(float& a, uint32_t w) {
+    // the four values of a word sum exactly (see the compensated form below)
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&lo));
+    float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&hi));
+    a = __fadd_rn(a, __fadd_rn(__fadd_rn(f0.x, f0.y), __fadd_rn(f1.x, f1.y)));
+}
+// Compensated FP8: every E4M3 value is an integer multiple of 2^-9 below 2^9,
+// so any sum of up to 64 of them is exact in binary32.  The four values of a
+// word are therefore added plainly (exactly), and one TwoSum carries the
+// word's total into the compensated accumulator.
+template <> __device__ __forceinline__ void acc_word<kDtFP8, Pair>(Pair& a, uint32_t w) {
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&lo));
+    float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&hi));
+    acc_add_f(a, __fadd_rn(__fadd_rn(f0.x, f0.y), __fadd_rn(f1.x, f1.y)));
+}
 
 // One scalar element at index i of the input (head / tail of the vector body).
 template <int DT, class A> __device__ __forceinline__ void acc_elem(A& a, const unsigned char* x, int64_t i);

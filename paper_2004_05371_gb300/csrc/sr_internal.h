@@ -89,7 +89,9 @@ inline int elem_size(int dtype) { return dtype == SR_BF16 ? 2 : (dtype == SR_FP8
 int reduce_validate(const void* x, int64_t n, int dtype, const void* out, const sr_config& cfg);
 int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& cfg, const DeviceInfo& d, Plan* p);
 int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, const Workspace& ws,
-                  cudaStream_t s);
+                  cudaStream_t s, bool skip_final = false);
+// Second kernel of the two-kernel form over `units` partial slots of ws.
+int reduce_launch_final(const Plan& p, int units, void* out, const Workspace& ws, cudaStream_t s);
 
 // Segmented sum (sr_segmented.cu)
 int seg_validate(const void* x, const int64_t* offsets, int64_t nseg, int dtype, const void* out,

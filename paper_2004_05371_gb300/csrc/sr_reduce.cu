@@ -155,7 +155,7 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
 }
 
 int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, const Workspace& ws,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool skip_final) {
     KernelSet ks;
     if (!kernels_for(p, &ks)) return SR_ERR_UNSUPPORTED;
 
@@ -228,7 +228,7 @@ int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, 
     e = cudaLaunchKernelExC(&lc, ks.main, args);
     if (e != cudaSuccess) return status_from_cuda(e);
 
-    if (p.stage == SR_TWO_KERNEL) {
+    if (p.stage == SR_TWO_KERNEL && !skip_final) {
         // The implicit barrier: stream order makes kernel 2 wait for every
         // CTA of kernel 1 (Section III-B-2).
         const int threads = std::min(1024, std::max(32, ((p.units + 31) / 32) * 32));
@@ -240,6 +240,22 @@ int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, 
         if (e != cudaSuccess) return status_from_cuda(e);
     }
     return SR_OK;
+}
+
+int reduce_launch_final(const Plan& p, int units, void* out, const Workspace& ws, cudaStream_t s) {
+    KernelSet ks;
+    if (!kernels_for(p, &ks)) return SR_ERR_UNSUPPORTED;
+    KParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.out = out;
+    kp.partials = ws.partials;
+    kp.scale = p.scale;
+    kp.fp64 = p.fp64 ? 1 : 0;
+    kp.units = units;
+    void* args[] = {&kp};
+    const int threads = std::min(1024, std::max(32, ((units + 31) / 32) * 32));
+    cudaError_t e = cudaLaunchKernel(ks.final, dim3(1), dim3(threads), args, 0, s);
+    return e == cudaSuccess ? SR_OK : status_from_cuda(e);
 }
 
 }  // namespace sr

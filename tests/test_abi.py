@@ -163,3 +163,15 @@ def test_analytic_selector_is_eq2(lib):
         n = int(N) // 4
         i, _ = sr.select_analytic(p, n, sr.F32, 1, cands)
         assert (i == 0) == model.prefer_basic(n * 4, p.mem_latency_ns, t_sync, thr_b, thr_m), N
+
+
+def test_host_entry_rejects_without_gpu(lib):
+    import numpy as np
+    x = np.zeros(16, np.float32)
+    out = np.zeros(1, np.float64)
+    xp, op = x.ctypes.data, out.ctypes.data
+    assert sr.reduce_sum_host_ptr(xp, 16, sr.F32, 0, None, stream=0) == sr.ERR_ARG
+    assert sr.reduce_sum_host_ptr(xp, -1, sr.F32, op, None, stream=0) == sr.ERR_ARG
+    assert sr.reduce_sum_host_ptr(xp, 16, 8, op, None, stream=0) == sr.ERR_DTYPE
+    assert sr.reduce_sum_host_ptr(xp, 16, sr.F32, op, sr.make_config(sr.ATOMIC), stream=0) == sr.ERR_UNSUPPORTED
+    assert sr.reduce_sum_host_ptr(xp + 2, 4, sr.F32, op, None, stream=0) == sr.ERR_ARG
