@@ -420,7 +420,14 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
     od = torch.from_numpy(off).to(dev)
     out_b = torch.empty(nseg, dtype=torch.float32, device=dev)
     out_p = torch.empty(nseg, dtype=torch.float32, device=dev)
-    cfg = sr.make_config(sr.AUTO)
+    # the batched launch's tile (unroll), vector width, grid and grid stage come
+    # from the exhaustive autotuner, run on this workload
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cands = sr.candidates(sms, full=True)
+    us = sr.autotune(x.data_ptr(), n, sr.F32, out_b.data_ptr(), cands, reps=3, offsets_ptr=od.data_ptr(),
+                     nseg=nseg, stream=stream)
+    best = int(np.argmin(us))
+    cfg = cands[best]
     sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out_b.data_ptr(), cfg,
                                          stream.cuda_stream))
     g = sr.SegmentedGraph(x, od, out_b, cfg)
@@ -437,6 +444,10 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
         return a.elapsed_time(b) / reps
 
     batched_ms = time_it(lambda: g.launch(stream), 20)
+    dflt = sr.make_config(sr.AUTO)
+    default_us = time_it(lambda: sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32,
+                                                                      out_p.data_ptr(), dflt, stream.cuda_stream)),
+                         10) * 1e3
     xp, op = x.data_ptr(), out_p.data_ptr()
     lens = np.diff(off)
     plain_cfg = sr.make_config(sr.AUTO)
@@ -475,7 +486,9 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
             "speedup_vs_plain_eager": round(eager_ms / batched_ms, 2),
             "max_err_over_gate_batched": round(err_b, 4), "max_err_over_gate_plain": round(err_p, 4),
             "batched_config": {"stage": sr.STAGE_NAMES.get(r.variant & sr.STAGE_MASK), "grid": r.grid,
-                               "block": r.block_threads, "vec_bytes": r.vec_bytes, "unroll": r.unroll}}
+                               "block": r.block_threads, "vec_bytes": r.vec_bytes, "unroll": r.unroll,
+                               "chosen_by": "sr_autotune over %d candidates (%.0f us best, %.0f us default)"
+                                            % (len(cands), us[best], default_us)}}
 
 
 def end_to_end(sr, torch, dev, stream, x_host, args):
@@ -499,10 +512,20 @@ def end_to_end(sr, torch, dev, stream, x_host, args):
     for _ in range(k):
         step()
     dt = (time.perf_counter() - t0) / k
+    # the same call reading the pinned array in place over the CPU-GPU link
+    direct = None
+    dcfg = sr.make_config(sr.F_HOST_DIRECT)
+    if sr.reduce_sum_host_ptr(pinned.data_ptr(), n, sr.F32, res.data_ptr(), dcfg, sh) == sr.OK:
+        t1 = time.perf_counter()
+        for _ in range(k):
+            sr.check(sr.reduce_sum_host_ptr(pinned.data_ptr(), n, sr.F32, res.data_ptr(), dcfg, sh))
+        ddt = (time.perf_counter() - t1) / k
+        direct = {"gbs": round(n * 4 / ddt / 1e9, 2), "ms_per_step": round(ddt * 1e3, 3),
+                  "path": "sr_reduce_sum_host with SR_F_HOST_DIRECT (kernel reads pinned host memory in place)"}
     return {"value": round(n * 4 / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": n * 4,
             "d2h_bytes_per_step": 4, "ms_per_step": round(dt * 1e3, 3), "result": float(res.item()),
             "path": "sr_reduce_sum_host: pinned host input, 64 MiB chunks on two copy streams overlapped "
-                    "with the chunk reductions, final combine, 4-byte read-back"}
+                    "with the chunk reductions, final combine, 4-byte read-back", "direct_read": direct}
 
 
 if __name__ == "__main__":

@@ -207,7 +207,14 @@ def segmented_suite(args):
     x = torch.from_numpy(workloads.uniform_f32(n, seed=0)).cuda()
     od = torch.from_numpy(off).cuda()
     out = torch.empty(nseg, dtype=torch.float32, device="cuda")
-    cfg = sr.make_config(args.variant if args.variant is not None else sr.AUTO)
+    if args.variant is not None:
+        cfg = sr.make_config(args.variant)
+    else:  # tile / vector width / grid / stage from the exhaustive autotuner
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        cands = sr.candidates(sms, full=True)
+        us = sr.autotune(x.data_ptr(), n, sr.F32, out.data_ptr(), cands, reps=3, offsets_ptr=od.data_ptr(),
+                         nseg=nseg)
+        cfg = cands[int(np.argmin(us))]
     sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(), cfg))
     g = sr.SegmentedGraph(x, od, out, cfg)
     st = torch.cuda.current_stream()

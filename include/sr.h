@@ -84,6 +84,10 @@ typedef enum {
                                    binary64; `out` is then a double */
 #define SR_F_BULK 0x400         /* load path: TMA bulk copies (cp.async.bulk) into a
                                    shared-memory ring instead of 128/256-bit LDG */
+#define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
+                                   array in place over the CPU-GPU link (page-locked
+                                   memory, or any memory where the device accesses
+                                   pageable memory) instead of staging copies */
 
 typedef enum {
     SR_OK = 0,
@@ -147,6 +151,9 @@ int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant,
  * SR_AUTO / SR_TWO_KERNEL with optional SR_F_KAHAN / SR_F_FP64_COMBINE and
  * launch-shape fields; other stages or SR_F_BULK -> SR_ERR_UNSUPPORTED.
  * The first call on a stream allocates the staging buffers (128 MiB).
+ * With SR_F_HOST_DIRECT there is no staging: one reduction (LDG path, stage
+ * SR_LAST_BLOCK) reads x through its device mapping; SR_ERR_UNSUPPORTED when x
+ * is neither page-locked nor accessible as pageable memory on this device.
  * Errors: as sr_reduce_sum_ex. */
 int sr_reduce_sum_host(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg,
                        sr_stream_t stream);

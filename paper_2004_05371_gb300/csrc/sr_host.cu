@@ -70,12 +70,62 @@ int get_pipe(cudaStream_t s, size_t chunk, HostPipe** out) {
 
 using namespace sr;
 
+namespace {
+
+// The reduction reads the host array in place (no staging copies).
+int host_direct(const void* host_x, int64_t n, int dtype, void* host_out, sr_config c, sr_stream_t stream) {
+    const int stage = c.variant & SR_STAGE_MASK;
+    if ((stage != SR_AUTO && stage != SR_LAST_BLOCK) || (c.variant & SR_F_BULK)) return SR_ERR_UNSUPPORTED;
+    c.variant = (c.variant & ~(SR_STAGE_MASK | SR_F_HOST_DIRECT)) | SR_LAST_BLOCK;
+    const void* fake_out = reinterpret_cast<const void*>(uintptr_t(1) << 20);
+    int st = reduce_validate(host_x, n, dtype, fake_out, c);
+    if (st != SR_OK) return st;
+    const DeviceInfo* d = current_device(&st);
+    if (!d) return st;
+    const void* dx = host_x;
+    if (n > 0) {
+        cudaPointerAttributes a;
+        cudaError_t e = cudaPointerGetAttributes(&a, host_x);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        if (a.type == cudaMemoryTypeHost) {
+            void* mapped = nullptr;
+            e = cudaHostGetDevicePointer(&mapped, const_cast<void*>(host_x), 0);
+            if (e != cudaSuccess) return status_from_cuda(e);
+            dx = mapped;
+        } else if (a.type == cudaMemoryTypeUnregistered) {
+            int pageable = 0;
+            e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, d->dev);
+            if (e != cudaSuccess) return status_from_cuda(e);
+            if (!pageable) return SR_ERR_UNSUPPORTED;
+        } else {
+            return SR_ERR_ARG;  // device or managed memory: use sr_reduce_sum_ex
+        }
+    }
+    Plan p;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = reduce_plan(dx, n, dtype, c, *d, &p);
+    if (st != SR_OK) return st;
+    Workspace ws;
+    st = get_workspace(s, &ws);
+    if (st != SR_OK) return st;
+    unsigned char* dev_out = ws.base + 192;
+    st = reduce_launch(dx, dev_out, p, *d, ws, s);
+    if (st != SR_OK) return st;
+    const size_t out_bytes = (dtype == SR_I32 || p.fp64) ? 8 : 4;
+    cudaError_t e = cudaMemcpyAsync(host_out, dev_out, out_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? SR_OK : status_from_cuda(e);
+}
+
+}  // namespace
+
 extern "C" int sr_reduce_sum_host(const void* host_x, int64_t n, int dtype, void* host_out, const sr_config* cfg,
                                   sr_stream_t stream) {
     sr_config c;
     std::memset(&c, 0, sizeof c);
     if (cfg) c = *cfg;
     if (host_out == nullptr) return SR_ERR_ARG;
+    if (c.variant & SR_F_HOST_DIRECT) return host_direct(host_x, n, dtype, host_out, c, stream);
     const int stage = c.variant & SR_STAGE_MASK;
     if (stage != SR_AUTO && stage != SR_TWO_KERNEL) return SR_ERR_UNSUPPORTED;
     if (c.variant & SR_F_BULK) return SR_ERR_UNSUPPORTED;

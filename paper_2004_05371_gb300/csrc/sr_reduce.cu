@@ -9,7 +9,8 @@ namespace sr {
 
 namespace {
 
-constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK;
+constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK |
+                            SR_F_HOST_DIRECT;
 // Arrays up to this many bytes take the single-cluster form under SR_AUTO:
 // one launch, no grid stage (its cost is launch latency, not bandwidth).
 constexpr int64_t kAutoSingleClusterBytes = 256 << 10;

@@ -32,9 +32,8 @@ template <> struct SegElem<kDtBF16> { static constexpr int v = 2; };
 template <> struct SegElem<kDtFP8> { static constexpr int v = 1; };
 
 // ------------------------------------------------------------ helpers
-// First s in [0, nseg] with offsets[s] >= key (nseg if none), for two keys
-// at once (their loads overlap).  Warp-wide: each round, 32 samples per key
-// shrink its interval 32-fold.
+// First s in [0, nseg] with offsets[s] >= key (nseg if none).  Warp-wide:
+// each round, 32 samples shrink the interval 32-fold.
 __device__ __forceinline__ void lb_round(const int64_t* off, int64_t key, int lane, int64_t& lo, int64_t& hi) {
     if (hi - lo <= 32) return;
     const int64_t step = (hi - lo + 31) / 32;
@@ -60,15 +59,10 @@ __device__ __forceinline__ int64_t lb_final(const int64_t* off, int64_t key, int
     const int64_t r = lo + (__ffs(m) - 1);
     return r < hi ? r : hi;
 }
-__device__ __forceinline__ void warp_lower_bound2(const int64_t* off, int64_t nseg, int64_t ka, int64_t kb, int lane,
-                                                  int64_t* ra, int64_t* rb) {
-    int64_t loa = 0, hia = nseg, lob = 0, hib = nseg;  // answers in [lo, hi]
-    while (hia - loa > 32 || hib - lob > 32) {
-        lb_round(off, ka, lane, loa, hia);
-        lb_round(off, kb, lane, lob, hib);
-    }
-    *ra = lb_final(off, ka, lane, loa, hia);
-    *rb = lb_final(off, kb, lane, lob, hib);
+__device__ __forceinline__ int64_t warp_lower_bound(const int64_t* off, int64_t nseg, int64_t key, int lane) {
+    int64_t lo = 0, hi = nseg;  // answer in [lo, hi]
+    while (hi - lo > 32) lb_round(off, key, lane, lo, hi);
+    return lb_final(off, key, lane, lo, hi);
 }
 
 // Sum of x[a, b) by one warp; the result is valid in lane 0.
@@ -210,9 +204,10 @@ __global__ void __launch_bounds__(1024) seg_kernel(const SegParams p) {
     const int64_t lo = base + (w * E < N ? w * E : N);
     const int64_t hi = base + ((w + 1) * E < N ? (w + 1) * E : N);
 
-    int64_t s_begin, s_end;
-    warp_lower_bound2(p.offsets, p.nseg, base + w * E, base + (w + 1) * E, lane, &s_begin, &s_end);
-    if (w == Wn - 1) s_end = p.nseg;
+    // first segment starting at or after this piece; the owned segments are
+    // those that start before the next piece (all remaining ones for the last warp)
+    const int64_t s_begin = warp_lower_bound(p.offsets, p.nseg, base + w * E, lane);
+    const int64_t next_lo = (w == Wn - 1) ? INT64_MAX : base + (w + 1) * E;
 
     // continuation of the segment that started before this piece
     if (lo < hi && s_begin > 0) {
@@ -234,11 +229,16 @@ __global__ void __launch_bounds__(1024) seg_kernel(const SegParams p) {
 
     // segments owned by this warp, offsets fetched 32 at a time
     int64_t spanning = -1;
-    for (int64_t s0 = s_begin; s0 < s_end; s0 += 32) {
-        const int64_t cnt = (s_end - s0) < 32 ? (s_end - s0) : 32;
+    bool more = true;
+    for (int64_t s0 = s_begin; more && s0 < p.nseg; s0 += 32) {
+        const int64_t cnt = (p.nseg - s0) < 32 ? (p.nseg - s0) : 32;
         const int64_t my_end = (lane < cnt) ? __ldg(p.offsets + s0 + lane + 1) : 0;
         int64_t start = __ldg(p.offsets + s0);
         for (int k = 0; k < cnt; ++k) {
+            if (start >= next_lo) {  // this segment belongs to the next piece
+                more = false;
+                break;
+            }
             const int64_t end = __shfl_sync(0xffffffffu, my_end, k);
             const int64_t s = s0 + k;
             const int64_t e = end < hi ? end : hi;

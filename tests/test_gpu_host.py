@@ -38,3 +38,23 @@ def test_host_entry_flags_and_repeat(sr):
         vals.add(float(out[0]))
         assert abs(float(out[0]) - S) / abs(S) <= 1e-6
     assert len(vals) == 1
+
+
+def test_host_direct_reads(sr):
+    """SR_F_HOST_DIRECT: the kernel reads page-locked host memory in place."""
+    n = (1 << 24) + 3
+    x = workloads.uniform_f32(n, seed=9)
+    xi = workloads.uniform_i32(n, seed=9)
+    pinned = torch.from_numpy(x).pin_memory()
+    pinned_i = torch.from_numpy(xi).pin_memory()
+    out = np.zeros(1, np.float32)
+    outi = np.zeros(1, np.int64)
+    cfg = sr.make_config(sr.F_HOST_DIRECT)
+    sr.check(sr.reduce_sum_host_ptr(pinned.data_ptr(), n, sr.F32, out.ctypes.data, cfg))
+    ex = oracle.to_float(oracle.exact_f32(x))
+    assert abs(float(out[0]) - ex) <= oracle.stated_fp32_bound(oracle.sum_abs_f32(x))
+    sr.check(sr.reduce_sum_host_ptr(pinned_i.data_ptr() + 4, n - 1, sr.I32, outi.ctypes.data, cfg))
+    assert int(outi[0]) == oracle.sum_i32(xi[1:])
+    # device memory is not a host array
+    d = torch.from_numpy(x).cuda()
+    assert sr.reduce_sum_host_ptr(d.data_ptr(), n, sr.F32, out.ctypes.data, cfg) == sr.ERR_ARG
