@@ -323,6 +323,7 @@ typedef struct sr_mlp_s* sr_mlp;
 int sr_mlp_create(int in_dim, int hidden, int out_dim, sr_mlp* mlp);   /* parameters start at 0 */
 int sr_mlp_destroy(sr_mlp mlp);
 int64_t sr_mlp_param_count(sr_mlp mlp);
+int sr_mlp_dims(sr_mlp mlp, int* in_dim, int* hidden, int* out_dim);
 /* Host copies of the parameters (count must equal sr_mlp_param_count);
  * set also resets the Adam state.  Synchronous. */
 int sr_mlp_set_params(sr_mlp mlp, const float* host_params, int64_t count);
@@ -339,6 +340,32 @@ int sr_mlp_train_step(sr_mlp mlp, const float* X, const float* Q, int batch, flo
 /* Inference kernel: cls[b] = argmax_o logits (lowest index on ties) for a
  * device batch X [batch][in_dim]; logits (device, optional) receives z. */
 int sr_mlp_predict(sr_mlp mlp, const float* X, int batch, int* cls, float* logits, sr_stream_t stream);
+
+/* Per-call selection.  A selector wraps a trained MLP (in_dim must be
+ * SR_SELECTOR_FEATURES, out_dim = ncand), its feature normalisation
+ * (x - mu) / sd and the candidate list its classes index (normally
+ * sr_candidates(0, sms, ...)).  The MLP stays owned by the caller and must
+ * outlive the selector. */
+typedef struct sr_selector_s* sr_selector;
+int sr_selector_create(sr_mlp mlp, const float* mu, const float* sd, const sr_config* cands, int ncand,
+                       sr_selector* selector);
+int sr_selector_destroy(sr_selector selector);
+/* The configuration for a call shape: memoised per (device, n, dtype, nseg,
+ * segment statistics at 1/16-octave resolution); on a miss the inference
+ * kernel runs on `stream` and the call waits for its one-int result. */
+int sr_selector_choose(sr_selector selector, int64_t n, int dtype, int64_t nseg, double len_mean, double len_std,
+                       double len_max, sr_config* cfg, sr_stream_t stream);
+/* Sums whose launch configuration is chosen per call: by `selector`, or —
+ * selector == NULL, the fallback — by exhaustive autotuning over the 40
+ * candidates on the call's own data the first time its shape is seen
+ * (memoised; that first call synchronises `stream`).  Other arguments and
+ * errors as sr_reduce_sum_ex / sr_reduce_sum_segmented_ex; the segmented form
+ * takes the segment-length statistics from the caller (n = mean * nseg). */
+int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int dtype, void* out,
+                           sr_stream_t stream);
+int sr_reduce_sum_segmented_selected(sr_selector selector, const void* x, const int64_t* offsets, int64_t nseg,
+                                     int dtype, void* out, double len_mean, double len_std, double len_max,
+                                     sr_stream_t stream);
 
 /* ------------------------------------------------- allocation-free sum */
 

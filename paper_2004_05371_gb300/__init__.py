@@ -146,6 +146,21 @@ def load():
                                        ctypes.POINTER(ctypes.c_float)]
     L.sr_reduce_sum_host.restype = i32
     L.sr_reduce_sum_host.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
+    L.sr_mlp_dims.restype = i32
+    L.sr_mlp_dims.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.sr_selector_create.restype = i32
+    L.sr_selector_create.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(Config), i32, ctypes.POINTER(vp)]
+    L.sr_selector_destroy.restype = i32
+    L.sr_selector_destroy.argtypes = [vp]
+    L.sr_selector_choose.restype = i32
+    L.sr_selector_choose.argtypes = [vp, i64, i32, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(Config), vp]
+    L.sr_reduce_sum_selected.restype = i32
+    L.sr_reduce_sum_selected.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.sr_reduce_sum_segmented_selected.restype = i32
+    L.sr_reduce_sum_segmented_selected.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_double, vp]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -417,6 +432,52 @@ def selector_features(n: int, dtype: int, nseg: int, len_mean: float, len_std: f
     check(lib().sr_selector_features(int(n), int(dtype), int(nseg), float(len_mean), float(len_std),
                                      float(len_max), out), "sr_selector_features")
     return list(out)
+
+
+class NativeSelector:
+    """sr_selector: a trained MLP + normalisation + candidate table, used by
+    sr_reduce_sum_selected.  Keeps the MLP alive."""
+
+    def __init__(self, mlp, mu, sd, cands):
+        self.mlp, self.cands = mlp, cands
+        f = ctypes.c_float * 9
+        self._mu, self._sd = f(*[float(v) for v in mu]), f(*[float(v) for v in sd])
+        self.h = ctypes.c_void_p()
+        check(lib().sr_selector_create(mlp.h, self._mu, self._sd, cands, len(cands), ctypes.byref(self.h)),
+              "sr_selector_create")
+
+    def choose(self, n, dtype, nseg=1, mean=None, std=0.0, mx=None, stream=None) -> Config:
+        c = Config()
+        mean = float(n) if mean is None else mean
+        mx = float(n) if mx is None else mx
+        check(lib().sr_selector_choose(self.h, int(n), int(dtype), int(nseg), float(mean), float(std), float(mx),
+                                       ctypes.byref(c), ctypes.c_void_p(_stream(stream))), "sr_selector_choose")
+        return c
+
+    def close(self):
+        if self.h:
+            lib().sr_selector_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reduce_sum_selected_ptr(selector, x_ptr, n, dtype, out_ptr, stream=None) -> int:
+    h = selector.h if selector is not None else None
+    return lib().sr_reduce_sum_selected(h, ctypes.c_void_p(x_ptr), int(n), int(dtype), ctypes.c_void_p(out_ptr),
+                                        ctypes.c_void_p(_stream(stream)))
+
+
+def reduce_sum_segmented_selected_ptr(selector, x_ptr, offsets_ptr, nseg, dtype, out_ptr, mean, std, mx,
+                                      stream=None) -> int:
+    h = selector.h if selector is not None else None
+    return lib().sr_reduce_sum_segmented_selected(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(offsets_ptr),
+                                                  int(nseg), int(dtype), ctypes.c_void_p(out_ptr), float(mean),
+                                                  float(std), float(mx), ctypes.c_void_p(_stream(stream)))
 
 
 def plan(n: int, dtype: int, config: Config = None) -> Config:

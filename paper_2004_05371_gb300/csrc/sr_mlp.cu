@@ -273,6 +273,14 @@ int sr_mlp_destroy(sr_mlp h) {
 
 int64_t sr_mlp_param_count(sr_mlp h) { return h ? h->d.P : -SR_ERR_ARG; }
 
+int sr_mlp_dims(sr_mlp h, int* in_dim, int* hidden, int* out_dim) {
+    if (!h || !in_dim || !hidden || !out_dim) return SR_ERR_ARG;
+    *in_dim = h->d.in;
+    *hidden = h->d.h;
+    *out_dim = h->d.out;
+    return SR_OK;
+}
+
 int sr_mlp_set_params(sr_mlp h, const float* host, int64_t count) {
     if (!h || !host || count != h->d.P) return SR_ERR_ARG;
     cudaError_t e = cudaMemcpy(h->params, host, sizeof(float) * count, cudaMemcpyHostToDevice);

@@ -1,0 +1,176 @@
+// Per-call launch selection: a trained MLP (served by its inference kernel)
+// or, without one, exhaustive autotuning on the call's own data — both
+// memoised per call shape, so a shape pays the choice once.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "sr_internal.h"
+
+namespace sr {
+namespace {
+
+using ShapeKey = std::tuple<int, int64_t, int, int64_t, int64_t, int64_t, int64_t>;  // dev, n, dtype, nseg, stats
+
+ShapeKey make_key(int dev, int64_t n, int dtype, int64_t nseg, double mean, double sd, double mx) {
+    // segment statistics enter at 1/16-octave resolution
+    auto q = [](double v) { return (int64_t)std::llround(16.0 * std::log2(1.0 + v)); };
+    return ShapeKey(dev, n, dtype, nseg, q(mean), q(sd), q(mx));
+}
+
+std::mutex g_tune_mu;
+std::map<ShapeKey, sr_config> g_tuned;  // autotuner fallback memo
+
+int current_dev(int* dev) {
+    cudaError_t e = cudaGetDevice(dev);
+    return e == cudaSuccess ? SR_OK : status_from_cuda(e);
+}
+
+}  // namespace
+}  // namespace sr
+
+using namespace sr;
+
+struct sr_selector_s {
+    sr_mlp mlp = nullptr;
+    float mu[SR_SELECTOR_FEATURES];
+    float sd[SR_SELECTOR_FEATURES];
+    std::vector<sr_config> cands;
+    float* d_x = nullptr;  // device feature row
+    int* d_cls = nullptr;  // device class
+    std::mutex mu_memo;
+    std::map<ShapeKey, int> memo;
+};
+
+extern "C" {
+
+int sr_selector_create(sr_mlp mlp, const float* mu, const float* sd, const sr_config* cands, int ncand,
+                       sr_selector* out) {
+    if (!mlp || !mu || !sd || !cands || ncand < 2 || !out) return SR_ERR_ARG;
+    *out = nullptr;
+    int din = 0, dh = 0, dout = 0;
+    if (sr_mlp_dims(mlp, &din, &dh, &dout) != SR_OK || din != SR_SELECTOR_FEATURES || dout != ncand)
+        return SR_ERR_ARG;
+    sr_selector s = new sr_selector_s;
+    s->mlp = mlp;
+    for (int i = 0; i < SR_SELECTOR_FEATURES; ++i) {
+        s->mu[i] = mu[i];
+        s->sd[i] = sd[i] > 0.f ? sd[i] : 1.f;
+    }
+    s->cands.assign(cands, cands + ncand);
+    cudaError_t e = cudaMalloc(&s->d_x, sizeof(float) * SR_SELECTOR_FEATURES);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_cls, sizeof(int));
+    if (e != cudaSuccess) {
+        sr_selector_destroy(s);
+        return status_from_cuda(e);
+    }
+    *out = s;
+    return SR_OK;
+}
+
+int sr_selector_destroy(sr_selector s) {
+    if (!s) return SR_OK;
+    cudaFree(s->d_x);
+    cudaFree(s->d_cls);
+    delete s;  // the MLP stays owned by the caller
+    return SR_OK;
+}
+
+int sr_selector_choose(sr_selector s, int64_t n, int dtype, int64_t nseg, double len_mean, double len_std,
+                       double len_max, sr_config* out, sr_stream_t stream) {
+    if (!s || !out) return SR_ERR_ARG;
+    int dev = 0;
+    int st = current_dev(&dev);
+    if (st != SR_OK) return st;
+    const ShapeKey key = make_key(dev, n, dtype, nseg, len_mean, len_std, len_max);
+    {
+        std::lock_guard<std::mutex> lk(s->mu_memo);
+        auto it = s->memo.find(key);
+        if (it != s->memo.end()) {
+            *out = s->cands[it->second];
+            return SR_OK;
+        }
+    }
+    float f[SR_SELECTOR_FEATURES];
+    st = sr_selector_features(n, dtype, nseg, len_mean, len_std, len_max, f);
+    if (st != SR_OK) return st;
+    for (int i = 0; i < SR_SELECTOR_FEATURES; ++i) f[i] = (f[i] - s->mu[i]) / s->sd[i];
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(s->d_x, f, sizeof f, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    st = sr_mlp_predict(s->mlp, s->d_x, 1, s->d_cls, nullptr, stream);  // the inference kernel
+    if (st != SR_OK) return st;
+    int cls = 0;
+    e = cudaMemcpyAsync(&cls, s->d_cls, sizeof cls, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (cls < 0 || cls >= (int)s->cands.size()) return SR_ERR_ARG;  // model trained for another candidate set
+    {
+        std::lock_guard<std::mutex> lk(s->mu_memo);
+        s->memo[key] = cls;
+    }
+    *out = s->cands[cls];
+    return SR_OK;
+}
+
+// Fallback: exhaustive autotuning over the 40 candidates on this call's data.
+static int tuned_config(const void* x, int64_t n, const int64_t* offsets, int64_t nseg, int dtype, void* out,
+                        double mean, double sd, double mx, sr_config* cfg, sr_stream_t stream) {
+    int dev = 0;
+    int st = current_dev(&dev);
+    if (st != SR_OK) return st;
+    const ShapeKey key = make_key(dev, n, dtype, nseg, mean, sd, mx);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *cfg = it->second;
+            return SR_OK;
+        }
+    }
+    const DeviceInfo* d = current_device(&st);
+    if (!d) return st;
+    const int nc = sr_candidates(0, d->sms, nullptr, 0);
+    std::vector<sr_config> c(nc);
+    if (sr_candidates(0, d->sms, c.data(), nc) != nc) return SR_ERR_ARG;
+    std::vector<float> us(nc);
+    st = sr_autotune(x, n, offsets, nseg, dtype, out, c.data(), nc, 2, us.data(), stream);
+    if (st != SR_OK) return st;
+    int best = 0;
+    for (int i = 1; i < nc; ++i)
+        if (us[i] < us[best]) best = i;
+    if (!std::isfinite(us[best])) return SR_ERR_LAUNCH;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = c[best];
+    }
+    *cfg = c[best];
+    return SR_OK;
+}
+
+int sr_reduce_sum_selected(sr_selector s, const void* x, int64_t n, int dtype, void* out, sr_stream_t stream) {
+    if (n < 0) return SR_ERR_ARG;
+    sr_config c;
+    const double dn = (double)n;
+    int st = s ? sr_selector_choose(s, n, dtype, 1, dn, 0.0, dn, &c, stream)
+               : tuned_config(x, n, nullptr, 1, dtype, out, dn, 0.0, dn, &c, stream);
+    if (st != SR_OK) return st;
+    return sr_reduce_sum_ex(x, n, dtype, out, &c, stream);
+}
+
+int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t* offsets, int64_t nseg, int dtype,
+                                     void* out, double len_mean, double len_std, double len_max,
+                                     sr_stream_t stream) {
+    if (nseg < 1) return nseg == 0 ? SR_OK : SR_ERR_ARG;
+    const int64_t n = (int64_t)std::llround(len_mean * (double)nseg);
+    sr_config c;
+    int st = s ? sr_selector_choose(s, n, dtype, nseg, len_mean, len_std, len_max, &c, stream)
+               : tuned_config(x, n, offsets, nseg, dtype, out, len_mean, len_std, len_max, &c, stream);
+    if (st != SR_OK) return st;
+    return sr_reduce_sum_segmented_ex(x, offsets, nseg, dtype, out, &c, stream);
+}
+
+}  // extern "C"

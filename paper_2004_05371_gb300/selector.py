@@ -77,6 +77,11 @@ class Selector:
     def __init__(self, mlp, mu, sd):
         self.mlp, self.mu, self.sd = mlp, mu, sd
 
+    def native(self, cands):
+        """The C-ABI selector (sr_selector) for per-call choices."""
+        from . import NativeSelector
+        return NativeSelector(self.mlp, self.mu, self.sd, cands)
+
     def choose(self, X, device="cuda"):
         import torch
         Xn = torch.from_numpy(((X - self.mu) / self.sd).astype(np.float32)).to(device)

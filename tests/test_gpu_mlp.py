@@ -114,3 +114,41 @@ def test_learned_selector_beats_the_model_without_it(sr):
     print("mean regret: mlp %.4f  model %.4f" % (r_mlp.mean(), r_model.mean()))
     assert np.all(np.isfinite(r_mlp))
     assert r_mlp.mean() < r_model.mean()
+
+
+def test_selected_entry_points(sr):
+    """sr_reduce_sum_selected / _segmented_selected: with a selector (any class
+    maps to a valid candidate) and with the autotuner fallback (selector NULL),
+    results match the oracle and choices are memoised per shape."""
+    from paper_2004_05371_gb300 import selector
+    import oracle
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cands = sr.candidates(sms)
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(512, 9)).astype(np.float32)
+    Q = np.eye(40, dtype=np.float32)[rng.integers(0, 40, 512)]
+    sel, _ = selector.train(X, Q, steps=50)
+    nat = sel.native(cands)
+    for n in (1000, (1 << 20) + 3, 1 << 24):
+        x = workloads.uniform_i32(n, seed=n)
+        xd = torch.from_numpy(x).cuda()
+        out = torch.zeros((), dtype=torch.int64, device="cuda")
+        for s in (nat, None):
+            for _ in range(2):
+                out.fill_(-1)
+                sr.check(sr.reduce_sum_selected_ptr(s, xd.data_ptr(), n, sr.I32, out.data_ptr()))
+                assert int(out.item()) == oracle.sum_i32(x)
+        c1 = nat.choose(n, sr.I32)
+        c2 = nat.choose(n, sr.I32)
+        assert (c1.variant, c1.grid, c1.vec_bytes) == (c2.variant, c2.grid, c2.vec_bytes)
+        assert any((c1.variant, c1.grid, c1.vec_bytes) == (c.variant, c.grid, c.vec_bytes) for c in cands)
+    off = workloads.segment_offsets(500, 1 << 22, seed=4, median=2048, sigma=1.5, hi=1 << 20)
+    x = workloads.uniform_i32(int(off[-1]), seed=4)
+    lens = np.diff(off).astype(np.float64)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
+    out = torch.zeros(500, dtype=torch.int64, device="cuda")
+    for s in (nat, None):
+        sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), 500, sr.I32, out.data_ptr(),
+                                                      lens.mean(), lens.std(), lens.max()))
+        assert np.array_equal(out.cpu().numpy(), oracle.segsum_i32(x, off))
+    nat.close()
