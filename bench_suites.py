@@ -163,29 +163,63 @@ def precision_suite(args):
 
 
 def sweep_suite(args):
+    """Device time per call, from CUDA graphs of back-to-back calls (no host
+    launch cost): warm = the same input every call; cold = each call preceded
+    by a 256 MiB buffer write (L2 flush), the flush-only graph's time
+    subtracted."""
     import torch
     import paper_2004_05371_gb300 as sr
     sr.load()
-    st = torch.cuda.current_stream()
     big = torch.empty(1 << 30, dtype=torch.float32, device="cuda").uniform_(-1, 1)
     bigi = big.view(torch.int32)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+
+    def graph_time(body, calls):
+        with torch.cuda.stream(s):
+            body()                       # warm-up (allocates the stream's workspace)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(calls):
+                body()
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / (3 * calls)   # ms per call
+
+    fl_ms = graph_time(lambda: flush.fill_(1), 20)
     for dt, src in (("f32", big), ("i32", bigi)):
         for k in range(10, 31, 2):
             n = 1 << k
             x = src[:n]
+            calls = 200 if k <= 20 else (20 if k <= 26 else 4)
             for name, v in (("auto", sr.AUTO), ("two_kernel", sr.TWO_KERNEL), ("atomic", sr.ATOMIC),
                             ("last_block", sr.LAST_BLOCK), ("grid_sync", sr.GRID_SYNC),
-                            ("single_cluster_16", sr.SINGLE_CLUSTER | sr.CLUSTER(4)),
-                            ("last_block_cluster4", sr.LAST_BLOCK | sr.CLUSTER(2)),
+                            ("single_cluster_8", sr.SINGLE_CLUSTER | sr.CLUSTER(3)),
+                            ("single_cta", sr.SINGLE_CLUSTER), ("last_block_cluster4", sr.LAST_BLOCK | sr.CLUSTER(2)),
                             ("last_block_bulk", sr.LAST_BLOCK | sr.F_BULK)):
+                if name in ("single_cluster_8", "single_cta") and k > 24:
+                    continue
                 cfg = sr.make_config(v)
-                out = sr.reduce_sum(x, config=cfg)
-                warm = _time_calls(torch, lambda: sr.reduce_sum(x, config=cfg, out=out), 20, st)
-                # cold: overwrite L2 between calls (the flush write is timed separately and subtracted)
-                fl = _time_calls(torch, lambda: flush.fill_(1), 5, st)
-                both = _time_calls(torch, lambda: (flush.fill_(1), sr.reduce_sum(x, config=cfg, out=out)), 5, st)
-                cold = max(both - fl, 1e-6)
+                out = torch.empty((), dtype=torch.int64 if dt == "i32" else torch.float32, device="cuda")
+
+                def call():
+                    sr.check(sr.reduce_sum_ptr(x.data_ptr(), n, sr.I32 if dt == "i32" else sr.F32, out.data_ptr(),
+                                               cfg, torch.cuda.current_stream().cuda_stream))
+                try:
+                    warm = graph_time(call, calls)
+                    both = graph_time(lambda: (flush.fill_(1), call()), max(4, calls // 10))
+                except Exception as e:  # e.g. a launch form that stream capture does not accept
+                    _emit({"suite": "sweep", "dtype": dt, "log2n": k, "variant": name, "error": str(e)[:160]})
+                    torch.cuda.synchronize()
+                    continue
+                cold = max(both - fl_ms, 1e-6)
                 _emit({"suite": "sweep", "dtype": dt, "log2n": k, "variant": name,
                        "warm_us": round(warm * 1e3, 2), "cold_us": round(cold * 1e3, 2),
                        "warm_gbs": round(n * 4 / (warm * 1e-3) / 1e9, 1),
