@@ -4,7 +4,7 @@
               autotuning on held-out random shapes (regret), training from
               ~20,000 autotuner timings
   barrier   : synchronisation cost per level and shape (Section V / IX)
-  precision : 2^28-element lognormal / cancelling inputs in FP32, BF16 and FP8,
+  precision : 2^28-element lognormal / cancelling inputs in FP32, BF16 and FP8 (SR_AUTO),
               plain vs compensated vs compensated + FP64 combine: error against
               the exact sum and the FP64 oracle, and throughput
   sweep     : size sweep 2^10..2^30 for FP32 and int32, every grid stage
@@ -146,7 +146,7 @@ def precision_suite(args):
         S = oracle.to_float(exact)
         cond = sabs / abs(S) if S else float("inf")
         for mode, flags in (("plain", 0), ("kahan", sr.F_KAHAN), ("kahan+fp64", sr.F_KAHAN | sr.F_FP64_COMBINE)):
-            cfg = sr.make_config(sr.LAST_BLOCK | flags, scale=scale or 0.0)
+            cfg = sr.make_config(sr.AUTO | flags, scale=scale or 0.0)  # last-block-done at this size
             out = sr.reduce_sum(xd, config=cfg)
             got = float(out.item())
             ms = _time_calls(torch, lambda: sr.reduce_sum(xd, config=cfg, out=out), 10, st)

@@ -11,9 +11,31 @@ namespace {
 
 constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK |
                             SR_F_HOST_DIRECT;
-// Arrays up to this many bytes take the single-cluster form under SR_AUTO:
-// one launch, no grid stage (its cost is launch latency, not bandwidth).
-constexpr int64_t kAutoSingleClusterBytes = 256 << 10;
+// SR_AUTO's launch shapes, from graph-timed size sweeps and autotuner sweeps
+// on a GB300 (device time per call):
+//   <= 16 KiB : one CTA, no grid stage                       (1.8-2.0 us)
+//   <= 1 MiB  : one cluster of 8 CTAs, DSMEM merge, no grid stage (2.2-3.0 us)
+//   <= 64 MiB : two-kernel form, grid sized by the work      (3.5-15 us)
+//   larger    : last-block-done with the per-dtype shape below (HBM-bound)
+struct AutoShape {
+    int block, vec, unroll;
+    bool bulk;
+    int tile, stages;
+};
+constexpr int64_t kAutoOneCtaBytes = 16 << 10;
+constexpr int64_t kAutoClusterBytes = 1 << 20;
+constexpr int64_t kAutoTwoKernelBytes = 64 << 20;
+
+AutoShape auto_large_shape(int dtype, bool comp) {
+    if (comp) {
+        if (dtype == SR_F32) return {544, 16, 4, true, 32 << 10, 4};
+        if (dtype == SR_BF16) return {544, 16, 4, true, 64 << 10, 3};
+        return {1024, 16, 2, false, 0, 0};  // FP8: four values per word sum exactly
+    }
+    if (dtype == SR_BF16) return {512, 32, 2, false, 0, 0};
+    if (dtype == SR_FP8E4M3) return {1024, 16, 4, false, 0, 0};
+    return {512, 32, 8, false, 0, 0};  // FP32, int32
+}
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -68,19 +90,35 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
     p.stage = c.variant & SR_STAGE_MASK;
     p.log2c = (c.variant & SR_CLUSTER_MASK) >> SR_CLUSTER_SHIFT;
 
+    int def_block = 512, def_vec = 16, def_unroll = 4, def_tile = 32 << 10, def_stages = 6;
     if (p.stage == SR_AUTO) {
-        if (n * p.elem <= kAutoSingleClusterBytes) {
+        const int64_t bytes = n * p.elem;
+        const bool chosen_cluster = p.log2c != 0;
+        if (bytes <= kAutoClusterBytes) {
             p.stage = SR_SINGLE_CLUSTER;
-            if (p.log2c == 0) p.log2c = 3;
+            if (!chosen_cluster) p.log2c = bytes <= kAutoOneCtaBytes ? 0 : 3;
+        } else if (bytes <= kAutoTwoKernelBytes) {
+            p.stage = SR_TWO_KERNEL;
         } else {
             p.stage = SR_LAST_BLOCK;
+            if (!p.bulk && !chosen_cluster) {
+                const AutoShape a = auto_large_shape(dtype, p.comp);
+                p.bulk = a.bulk;
+                def_block = a.block;
+                def_vec = a.vec;
+                def_unroll = a.unroll;
+                if (a.bulk) {
+                    def_tile = a.tile;
+                    def_stages = a.stages;
+                }
+            }
         }
     }
     p.cluster = 1 << p.log2c;
 
-    p.vec = p.bulk ? 16 : (c.vec_bytes ? c.vec_bytes : 16);
-    p.unroll = c.unroll ? c.unroll : 4;
-    p.block = c.block_threads ? c.block_threads : (p.bulk ? 288 : 512);
+    p.vec = p.bulk ? 16 : (c.vec_bytes ? c.vec_bytes : def_vec);
+    p.unroll = c.unroll ? c.unroll : def_unroll;
+    p.block = c.block_threads ? c.block_threads : (p.bulk ? (def_block == 512 ? 288 : def_block) : def_block);
 
     // geometry: scalar head up to the vector alignment, vector body, scalar tail
     const int64_t per_vec = p.vec / p.elem;
@@ -94,8 +132,8 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
     int ctas_per_sm;
     int64_t work_ctas;
     if (p.bulk) {
-        p.tile = c.tile_bytes ? c.tile_bytes : (32 << 10);
-        p.stages = c.stages ? c.stages : 6;
+        p.tile = c.tile_bytes ? c.tile_bytes : def_tile;
+        p.stages = c.stages ? c.stages : def_stages;
         p.smem = (size_t)p.stages * p.tile + 16 * (size_t)p.stages;
         if (p.smem > (size_t)d.smem_per_block_optin) return SR_ERR_LAUNCH;
         p.body_bytes = p.nvec * 16;
