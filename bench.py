@@ -312,7 +312,10 @@ def main():
     peak, peak_kind = _peaks()
     kernel_ms = statistics.mean(per_launch_ms)
     achieved = bytes_step / (kernel_ms * 1e-3) / 1e9
-    kernel_tag = "reduce_%s" % ("bulk" if resolved.variant & sr.F_BULK else "ldg")
+    if resolved.variant & sr.F_BULK:
+        kernel_tag = "reduce_bulk_t%d_s%d" % (resolved.tile_bytes, resolved.stages)
+    else:
+        kernel_tag = "reduce_ldg_v%d_u%d" % (resolved.vec_bytes, resolved.unroll)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kernel_tag),
                 "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_kind
