@@ -398,6 +398,18 @@ int sr_reduce_sum_segmented_selected(sr_selector selector, const void* x, const 
 int sr_reduce_sum_noalloc(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg,
                           sr_stream_t stream);
 
+/* ------------------------------------------------------------ self-test */
+
+/* Failure-detection self-test (no counterpart in the paper): launches on
+ * `stream` one CTA that waits on an mbarrier nothing ever completes.  The
+ * wait is bounded by limit_ns of %globaltimer time (0 < limit_ns <= 10 s);
+ * when it gives up the kernel records SR_ERR_TIMEOUT in the stream's error
+ * word and returns, so the next sr_stream_status(stream) reports
+ * SR_ERR_TIMEOUT (and clears it) and the context stays usable.  This is the
+ * same bounded-wait path every mbarrier wait of the TMA load path takes
+ * (its limit: SR_SPIN_LIMIT_NS, default 2 s). */
+int sr_selftest_bounded_wait(uint64_t limit_ns, sr_stream_t stream);
+
 /* ------------------------------------------------------ host helpers */
 
 const char* sr_status_string(int status);

@@ -161,6 +161,8 @@ def load():
     L.sr_reduce_sum_segmented_selected.restype = i32
     L.sr_reduce_sum_segmented_selected.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.c_double, ctypes.c_double,
                                                    ctypes.c_double, vp]
+    L.sr_selftest_bounded_wait.restype = i32
+    L.sr_selftest_bounded_wait.argtypes = [ctypes.c_uint64, vp]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -489,3 +491,7 @@ def plan(n: int, dtype: int, config: Config = None) -> Config:
 
 def stream_status(stream=None) -> int:
     return lib().sr_stream_status(ctypes.c_void_p(_stream(stream)))
+
+
+def selftest_bounded_wait(limit_ns: int, stream=None) -> int:
+    return lib().sr_selftest_bounded_wait(int(limit_ns), ctypes.c_void_p(_stream(stream)))

@@ -257,11 +257,12 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
             }
             if (!ok) {
                 // Do not leave while copies may still be writing this CTA's
-                // shared memory: wait (bounded) for the last one issued into
-                // each stage.
+                // shared memory: wait for the last one issued into each stage,
+                // bounded separately (at least 1 s, whatever the spin limit).
+                const uint64_t drain = p.limit_ns > 1000000000ull ? p.limit_ns : 1000000000ull;
                 for (int64_t j = k - 1; j >= 0 && j >= k - S; --j) {
                     const int s = (int)(j % S);
-                    mbar_wait_bounded(full0 + 8u * s, (uint32_t)((j / S) & 1), p.limit_ns);
+                    mbar_wait_bounded(full0 + 8u * s, (uint32_t)((j / S) & 1), drain);
                 }
             }
         }

@@ -1,0 +1,36 @@
+"""Failure detection without a GPU fault: a device wait on a flag nothing sets
+expires by its own bound, the host reads SR_ERR_TIMEOUT, and the context
+keeps working."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_times_out_and_context_survives(sr):
+    s = torch.cuda.Stream()
+    assert sr.stream_status(s) == sr.OK
+    t0 = time.perf_counter()
+    assert sr.selftest_bounded_wait(20_000_000, s) == sr.OK      # 20 ms bound
+    assert sr.stream_status(s) == sr.ERR_TIMEOUT                 # synchronises, reads, clears
+    assert time.perf_counter() - t0 < 5.0
+    assert sr.stream_status(s) == sr.OK                          # cleared
+    # the context is intact: a full reduction on the same stream still matches the oracle
+    x = workloads.uniform_i32(1 << 22, seed=5)
+    xd = torch.from_numpy(x).cuda()
+    with torch.cuda.stream(s):
+        out = sr.reduce_sum(xd, variant=sr.LAST_BLOCK | sr.F_BULK, stream=s)
+    s.synchronize()
+    assert int(out.item()) == oracle.sum_i32(x)
+    assert sr.stream_status(s) == sr.OK
+
+
+def test_selftest_rejects_bad_limits(sr):
+    assert sr.selftest_bounded_wait(0) == sr.ERR_ARG
+    assert sr.selftest_bounded_wait(20_000_000_000) == sr.ERR_ARG

@@ -125,3 +125,36 @@ def test_fp64_combine_output_is_double(sr):
     x = _dev(workloads.uniform_f32(1 << 16, seed=3))
     out = sr.reduce_sum(x, variant=sr.LAST_BLOCK | sr.F_FP64_COMBINE)
     assert out.dtype == torch.float64
+
+
+@pytest.mark.slow
+def test_full_size_precision_workloads(sr):
+    """The precision workload at its full size (n = 2^28): lognormal(0, 4)
+    magnitudes with random signs in FP32, BF16 and FP8, plain / compensated /
+    compensated + FP64 combine (SR_AUTO launch shapes), and cancelling FP32
+    pairs at cond ~1e8 — every result inside its gate."""
+    n = 1 << 28
+    x = workloads.lognormal_f32(n, seed=0, sigma=4.0)
+    cases = [("f32", _dev(x), oracle.exact_f32(x), oracle.sum_abs_f32(x), {})]
+    bits = workloads.to_bf16_bits(x)
+    dec = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+    cases.append(("bf16", _bf16(bits), oracle.exact_bf16(bits), oracle.sum_abs_f32(dec), {}))
+    del dec
+    codes, deq = workloads.to_e4m3_codes(x)
+    cases.append(("fp8", _dev(codes), oracle.exact_e4m3(codes, deq), oracle.sum_e4m3(codes & 0x7F, deq),
+                  {"scale": deq}))
+    del x
+    for name, xd, exact, sabs, kw in cases:
+        S = oracle.to_float(exact)
+        got = _run(sr, xd, sr.AUTO, **kw)
+        assert abs(got - S) <= oracle.stated_fp32_bound(sabs), name
+        for flags in (sr.F_KAHAN, sr.F_KAHAN | sr.F_FP64_COMBINE):
+            got = _run(sr, xd, sr.AUTO | flags, **kw)
+            assert abs(got - S) <= _kahan_bound(n, sabs), (name, flags)
+            assert abs(got - S) / abs(S) <= 1e-6, (name, flags, got, S)   # cond ~ 43 here
+        del xd
+        torch.cuda.empty_cache()
+    xc = workloads.cancelling_f32(n, cond=1e8, seed=0)
+    S = oracle.to_float(oracle.exact_f32(xc))
+    got = _run(sr, _dev(xc), sr.AUTO | sr.F_KAHAN | sr.F_FP64_COMBINE)
+    assert abs(got - S) / abs(S) <= 1e-6, (got, S)
