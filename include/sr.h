@@ -188,8 +188,8 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * SR_LAST_BLOCK (default; per-segment tickets) or SR_ATOMIC (out zeroed
  * first; FP order not deterministic).  All other forms are deterministic.
  * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE),
- * block_threads, ctas_per_sm, grid (at most 65536 warps in total), vec_bytes,
- * unroll, scale (FP8).  SR_SINGLE_CLUSTER, cluster bits and SR_F_BULK ->
+ * block_threads (at most 512), ctas_per_sm, grid (at most 65536 warps in
+ * total), vec_bytes, unroll, scale (FP8).  SR_SINGLE_CLUSTER, cluster bits and SR_F_BULK ->
  * SR_ERR_UNSUPPORTED.
  * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,
  * bad config), SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */

@@ -65,48 +65,30 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int64_t* off, int64_t 
     return lb_final(off, key, lane, lo, hi);
 }
 
-// Sum of x[a, b) by one warp; the result is valid in lane 0.
-template <int DT, bool COMP, int VB, int UNROLL>
-__device__ __forceinline__ typename Acc<DT, COMP>::T warp_piece_sum(const unsigned char* x, int64_t a, int64_t b,
-                                                                    int lane) {
-    using A = typename Acc<DT, COMP>::T;
-    constexpr int EB = SegElem<DT>::v;
-    constexpr int PV = VB / EB;  // elements per vector
-    constexpr int W = VB / 4;
-    A acc[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) acc[w] = Op<A>::zero();
-    if (b > a) {
-        const uintptr_t addr = reinterpret_cast<uintptr_t>(x) + (uintptr_t)a * EB;
-        const int64_t head = (int64_t)(((uintptr_t)VB - addr % VB) % VB) / EB;
-        const int64_t va = a + (head < b - a ? head : b - a);
-        const int64_t nv = (b - va) / PV;
-        const int64_t tb = va + nv * PV;
-        if (a + lane < va) acc_elem<DT>(acc[0], x, a + lane);
-        const unsigned char* body = x + va * EB;
-        int64_t v = lane;
-        for (; v + (UNROLL - 1) * 32 < nv; v += UNROLL * 32) {
-            uint32_t r[UNROLL][W];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) ldg_vec(body + (v + u * 32) * VB, r[u]);
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u)
-#pragma unroll
-                for (int w = 0; w < W; ++w) acc_word<DT>(acc[w], r[u][w]);
-        }
-        for (; v < nv; v += 32) {
-            uint32_t r[W];
-            ldg_vec(body + v * VB, r);
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc_word<DT>(acc[w], r[w]);
-        }
-        if (tb + lane < b) acc_elem<DT>(acc[0], x, tb + lane);
-    }
-    A t = acc[0];
-#pragma unroll
-    for (int w = 1; w < W; ++w) t = Op<A>::add(t, acc[w]);
-    return warp_reduce(t);
+// Element j of a vector held as 32-bit words (the masked slow path; j is a
+// compile-time constant after unrolling).
+template <int DT, class A> __device__ __forceinline__ void acc_vec_elem(A& a, const uint32_t* r, int j);
+template <> __device__ __forceinline__ void acc_vec_elem<kDtI32, long long>(long long& a, const uint32_t* r, int j) {
+    a += (long long)(int)r[j];
 }
+template <class A> __device__ __forceinline__ void acc_vec_elem_f32(A& a, const uint32_t* r, int j) {
+    acc_add_f(a, __uint_as_float(r[j]));
+}
+template <class A> __device__ __forceinline__ void acc_vec_elem_bf16(A& a, const uint32_t* r, int j) {
+    const uint32_t w = r[j >> 1];
+    acc_add_f(a, __uint_as_float((j & 1) ? (w & 0xffff0000u) : (w << 16)));
+}
+template <class A> __device__ __forceinline__ void acc_vec_elem_fp8(A& a, const uint32_t* r, int j) {
+    const uint32_t w = r[j >> 2];
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)((w >> (8 * (j & 3))) & 0xffu), __NV_E4M3);
+    acc_add_f(a, __half2float(*reinterpret_cast<__half*>(&h)));
+}
+template <> __device__ __forceinline__ void acc_vec_elem<kDtF32, float>(float& a, const uint32_t* r, int j) { acc_vec_elem_f32(a, r, j); }
+template <> __device__ __forceinline__ void acc_vec_elem<kDtF32, Pair>(Pair& a, const uint32_t* r, int j) { acc_vec_elem_f32(a, r, j); }
+template <> __device__ __forceinline__ void acc_vec_elem<kDtBF16, float>(float& a, const uint32_t* r, int j) { acc_vec_elem_bf16(a, r, j); }
+template <> __device__ __forceinline__ void acc_vec_elem<kDtBF16, Pair>(Pair& a, const uint32_t* r, int j) { acc_vec_elem_bf16(a, r, j); }
+template <> __device__ __forceinline__ void acc_vec_elem<kDtFP8, float>(float& a, const uint32_t* r, int j) { acc_vec_elem_fp8(a, r, j); }
+template <> __device__ __forceinline__ void acc_vec_elem<kDtFP8, Pair>(Pair& a, const uint32_t* r, int j) { acc_vec_elem_fp8(a, r, j); }
 
 // ---------------------------------------------------- output and carries
 __device__ __forceinline__ void seg_out(const SegParams& p, int64_t s, long long v) {
@@ -189,10 +171,20 @@ template <class A> __device__ __forceinline__ void span_arrive(const SegParams& 
 }
 
 // ------------------------------------------------------------- main kernel
+// One warp walks its piece [lo, hi) in element order: a scalar head up to the
+// vector alignment, rows of 32 lane vectors (loads issued UNROLL rows ahead,
+// independently of where segments end), and a scalar tail.  The current
+// segment and its end travel with the walk; a row that contains no boundary
+// is accumulated whole, a row that does takes a masked per-element path and
+// emits each segment that ends in it — the load pipeline never drains at a
+// boundary.
 template <int DT, bool COMP, int VB, int UNROLL>
-__global__ void __launch_bounds__(1024) seg_kernel(const SegParams p) {
+__global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     using A = typename Acc<DT, COMP>::T;
-    constexpr int PV = VB / SegElem<DT>::v;
+    constexpr int EB = SegElem<DT>::v;
+    constexpr int PV = VB / EB;  // elements per lane vector
+    constexpr int W = VB / 4;    // 32-bit words per lane vector
+    constexpr int RW = 32 * PV;  // elements per row
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t Wn = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -203,61 +195,138 @@ __global__ void __launch_bounds__(1024) seg_kernel(const SegParams p) {
     if (E < PV) E = PV;
     const int64_t lo = base + (w * E < N ? w * E : N);
     const int64_t hi = base + ((w + 1) * E < N ? (w + 1) * E : N);
-
-    // first segment starting at or after this piece; the owned segments are
-    // those that start before the next piece (all remaining ones for the last warp)
-    const int64_t s_begin = warp_lower_bound(p.offsets, p.nseg, base + w * E, lane);
     const int64_t next_lo = (w == Wn - 1) ? INT64_MAX : base + (w + 1) * E;
 
-    // continuation of the segment that started before this piece
-    if (lo < hi && s_begin > 0) {
-        const int64_t cont_end = __ldg(p.offsets + s_begin);
-        if (cont_end > lo) {
-            const int64_t sp = s_begin - 1;
-            const int64_t e = cont_end < hi ? cont_end : hi;
-            A v = warp_piece_sum<DT, COMP, VB, UNROLL>(p.x, lo, e, lane);
-            const int64_t w_o = (__ldg(p.offsets + sp) - base) / E;
-            const int64_t w_e = (cont_end - 1 - base) / E;
-            if (p.stage == kStageAtomic) {
-                if (lane == 0) seg_atomic(p, sp, v);
-            } else {
-                if (lane == 0) carry_store(p, p.carry_first, w, v);
-                if (p.stage == kStageLastBlock) span_arrive<A>(p, sp, w_o, w_e, lane);
-            }
-        }
+    // geometry of the piece: scalar head [lo, a0), vector rows [a0, hi_al), scalar tail [hi_al, hi)
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(p.x) + (uintptr_t)lo * EB;
+    int64_t a0 = lo + (int64_t)(((uintptr_t)VB - addr % VB) % VB) / EB;
+    if (a0 > hi) a0 = hi;
+    const int64_t nvec = (hi - a0) / PV;
+    const int64_t hi_al = a0 + nvec * PV;
+    const int64_t nrows = (nvec + 31) / 32;
+    const unsigned char* body = p.x + a0 * EB;
+
+    // first batch of rows in flight before the segment search
+    uint32_t buf[UNROLL][W];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+        const int64_t v = (int64_t)u * 32 + lane;
+        if (v < nvec) ldg_vec(body + v * VB, buf[u]);
     }
 
-    // segments owned by this warp, offsets fetched 32 at a time
+    const int64_t s_begin = warp_lower_bound(p.offsets, p.nseg, base + w * E, lane);
+    // stream state (warp-uniform): segment `cur` = [cur_start, cur_end)
+    int64_t cur = s_begin;
+    if (lo < hi && s_begin > 0 && __ldg(p.offsets + s_begin) > lo) cur = s_begin - 1;  // continuation
+    int64_t wb = cur + 1;  // offsets window: lane k holds offsets[wb + k]
+    int64_t win = (wb + lane <= p.nseg) ? __ldg(p.offsets + wb + lane) : INT64_MAX;
+    int64_t cur_start = (cur < p.nseg) ? __ldg(p.offsets + cur) : INT64_MAX;
+    int64_t cur_end = (cur < p.nseg) ? __shfl_sync(0xffffffffu, win, 0) : INT64_MAX;
     int64_t spanning = -1;
-    bool more = true;
-    for (int64_t s0 = s_begin; more && s0 < p.nseg; s0 += 32) {
-        const int64_t cnt = (p.nseg - s0) < 32 ? (p.nseg - s0) : 32;
-        const int64_t my_end = (lane < cnt) ? __ldg(p.offsets + s0 + lane + 1) : 0;
-        int64_t start = __ldg(p.offsets + s0);
-        for (int k = 0; k < cnt; ++k) {
-            if (start >= next_lo) {  // this segment belongs to the next piece
-                more = false;
-                break;
+    A acc[W];  // one accumulator per 32-bit word of the lane vector
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[k] = Op<A>::zero();
+
+    // emit the current segment's piece and move to the next segment
+    auto emit_advance = [&]() {
+        A t = acc[0];
+#pragma unroll
+        for (int k = 1; k < W; ++k) t = Op<A>::add(t, acc[k]);
+        A v = warp_reduce(t);
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = Op<A>::zero();
+        const int64_t s = cur;
+        if (cur_start < lo) {  // continuation of a segment owned by an earlier warp
+            if (p.stage == kStageAtomic) {
+                if (lane == 0) seg_atomic(p, s, v);
+            } else {
+                if (lane == 0) carry_store(p, p.carry_first, w, v);
+                if (p.stage == kStageLastBlock)
+                    span_arrive<A>(p, s, (cur_start - base) / E, (cur_end - 1 - base) / E, lane);
             }
-            const int64_t end = __shfl_sync(0xffffffffu, my_end, k);
-            const int64_t s = s0 + k;
-            const int64_t e = end < hi ? end : hi;
-            A v = warp_piece_sum<DT, COMP, VB, UNROLL>(p.x, start, e, lane);
-            if (end <= hi) {
-                if (lane == 0) seg_out(p, s, v);
-            } else {  // runs past this piece: only the last owned segment can
-                spanning = s;
-                const int64_t w_e = (end - 1 - base) / E;
-                if (p.stage == kStageAtomic) {
-                    if (lane == 0) seg_atomic(p, s, v);
-                } else {
-                    if (lane == 0) carry_store(p, p.carry_last, w, v);
-                    if (p.stage == kStageLastBlock) span_arrive<A>(p, s, w, w_e, lane);
-                }
+        } else if (cur_end <= hi) {  // owned and complete
+            if (lane == 0) seg_out(p, s, v);
+        } else {  // owned, runs past this piece
+            spanning = s;
+            if (p.stage == kStageAtomic) {
+                if (lane == 0) seg_atomic(p, s, v);
+            } else {
+                if (lane == 0) carry_store(p, p.carry_last, w, v);
+                if (p.stage == kStageLastBlock) span_arrive<A>(p, s, w, (cur_end - 1 - base) / E, lane);
             }
-            start = end;
         }
+        cur += 1;
+        cur_start = cur_end;
+        if (cur >= p.nseg) {
+            cur_end = INT64_MAX;
+            return;
+        }
+        if (cur + 1 - wb >= 32) {
+            wb = cur + 1;
+            win = (wb + lane <= p.nseg) ? __ldg(p.offsets + wb + lane) : INT64_MAX;
+        }
+        cur_end = __shfl_sync(0xffffffffu, win, (int)(cur + 1 - wb));
+    };
+
+    // scalar chunk [c0, c1), at most 32 elements: lane l holds element c0 + l
+    auto scalar_chunk = [&](int64_t c0, int64_t c1) {
+        if (c0 >= c1) return;
+        while (cur_end <= c0) emit_advance();
+        const int64_t idx = c0 + lane;
+        A one = Op<A>::zero();
+        if (idx < c1) acc_elem<DT>(one, p.x, idx);
+        for (;;) {
+            if (idx < c1 && idx >= cur_start && idx < cur_end) acc[0] = Op<A>::add(acc[0], one);
+            if (cur_end >= c1) break;
+            emit_advance();
+        }
+    };
+
+    // row r of vectors, words in `r_words` (lane's vector)
+    auto row = [&](int64_t r, const uint32_t (&r_words)[W]) {
+        const int64_t c0 = a0 + r * RW;
+        const int64_t c1 = (c0 + RW < hi_al) ? c0 + RW : hi_al;
+        while (cur_end <= c0) emit_advance();
+        const int64_t e0 = c0 + (int64_t)lane * PV;
+        const bool valid = e0 < c1;
+        if (cur_end >= c1) {  // no boundary inside the row
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) acc_word<DT>(acc[k], r_words[k]);
+            }
+            return;
+        }
+        for (;;) {  // segments end inside this row
+            if (valid) {
+                // element j of the lane's vector belongs to the current segment
+                // when cur_start <= e0 + j < cur_end (static indices keep the
+                // vector in registers)
+#pragma unroll
+                for (int j = 0; j < PV; ++j)
+                    if (e0 + j >= cur_start && e0 + j < cur_end) acc_vec_elem<DT>(acc[j * W / PV], r_words, j);
+            }
+            if (cur_end >= c1) break;
+            emit_advance();
+        }
+    };
+
+    scalar_chunk(lo, a0);
+    for (int64_t r = 0; r < nrows; r += UNROLL) {
+        if (r > 0) {
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int64_t v = (r + u) * 32 + lane;
+                if (v < nvec) ldg_vec(body + v * VB, buf[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (r + u < nrows) row(r + u, buf[u]);
     }
+    scalar_chunk(hi_al, hi);
+    // the segment holding the piece's last element, then any (empty) segment
+    // this warp owns that starts at or after hi
+    while (cur < p.nseg && cur_start < next_lo) emit_advance();
 
     if (p.stage == kStageTwoKernel || p.stage == kStageGridSync) {
         if (lane == 0) p.last_seg[w] = spanning;

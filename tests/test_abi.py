@@ -98,7 +98,8 @@ def test_segmented_rejects_bad_arguments_without_gpu(lib):
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK) == sr.ERR_UNSUPPORTED
     assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1)) == sr.ERR_UNSUPPORTED
     assert call(block_threads=100) == sr.ERR_ARG
-    assert call(grid=100000, block_threads=1024) == sr.ERR_ARG     # more than 65536 warps
+    assert call(grid=100000, block_threads=512) == sr.ERR_ARG      # more than 65536 warps
+    assert call(block_threads=1024) == sr.ERR_ARG                  # segmented CTAs: at most 512 threads
     assert call(nseg=0, x=0, off=0, out=0) == sr.OK                 # nothing to do, nothing launched
 
 

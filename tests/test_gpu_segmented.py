@@ -64,7 +64,8 @@ def test_random_layouts(sr, stage, nseg, max_len):
 
 
 @pytest.mark.parametrize("stage", STAGES)
-@pytest.mark.parametrize("vec,unroll,block", [(16, 1, 32), (16, 4, 256), (32, 2, 512), (32, 8, 1024), (16, 8, 128)])
+@pytest.mark.parametrize("vec,unroll,block", [(16, 1, 32), (16, 4, 256), (32, 2, 512), (32, 8, 512), (16, 8, 128),
+                                              (32, 8, 256)])
 def test_launch_shapes(sr, stage, vec, unroll, block):
     off = workloads.segment_offsets(300, 1 << 20, seed=5, median=1024, sigma=2.0, hi=1 << 18)
     n = int(off[-1])
