@@ -167,6 +167,13 @@ int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out,
  * bounded wait expired, else SR_OK (or SR_ERR_CUDA). */
 int sr_stream_status(sr_stream_t stream);
 
+/* Synchronise `stream`, then free the library's workspace and host-entry
+ * staging buffers for (current device, stream); a later call on the stream
+ * allocates them again.  Call it before destroying a stream the library
+ * was used on (otherwise they live until the process exits).  Pending
+ * error flags of the stream are discarded with the workspace. */
+int sr_stream_release(sr_stream_t stream);
+
 /* Resolve the launch shape the library would use for this call on the
  * current device, without launching: fills *resolved (variant with the
  * stage chosen, block_threads, grid, vec_bytes, unroll, tile_bytes, stages).

@@ -163,6 +163,8 @@ def load():
                                                    ctypes.c_double, vp]
     L.sr_selftest_bounded_wait.restype = i32
     L.sr_selftest_bounded_wait.argtypes = [ctypes.c_uint64, vp]
+    L.sr_stream_release.restype = i32
+    L.sr_stream_release.argtypes = [vp]
     L.sr_stream_status.restype = i32
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
@@ -495,3 +497,7 @@ def stream_status(stream=None) -> int:
 
 def selftest_bounded_wait(limit_ns: int, stream=None) -> int:
     return lib().sr_selftest_bounded_wait(int(limit_ns), ctypes.c_void_p(_stream(stream)))
+
+
+def stream_release(stream=None) -> int:
+    return lib().sr_stream_release(ctypes.c_void_p(_stream(stream)))

@@ -373,6 +373,14 @@ int sr_stream_status(sr_stream_t stream) {
     return SR_OK;
 }
 
+int sr_stream_release(sr_stream_t stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    release_workspace((cudaStream_t)stream);
+    release_host_pipe((cudaStream_t)stream);
+    return SR_OK;
+}
+
 const char* sr_status_string(int s) {
     switch (s) {
     case SR_OK: return "SR_OK";

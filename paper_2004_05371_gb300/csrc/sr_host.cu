@@ -66,6 +66,24 @@ int get_pipe(cudaStream_t s, size_t chunk, HostPipe** out) {
 }
 
 }  // namespace
+
+void release_host_pipe(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_hp_mu);
+    auto it = g_pipes.find(std::make_pair(dev, s));
+    if (it == g_pipes.end()) return;
+    HostPipe& p = it->second;
+    for (int b = 0; b < 2; ++b) {
+        if (p.copy[b]) cudaStreamSynchronize(p.copy[b]);
+        if (p.stage[b]) cudaFree(p.stage[b]);
+        if (p.copy[b]) cudaStreamDestroy(p.copy[b]);
+        if (p.copied[b]) cudaEventDestroy(p.copied[b]);
+        if (p.consumed[b]) cudaEventDestroy(p.consumed[b]);
+    }
+    g_pipes.erase(it);
+}
+
 }  // namespace sr
 
 using namespace sr;

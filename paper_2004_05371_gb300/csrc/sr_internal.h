@@ -76,6 +76,7 @@ int status_from_cuda(cudaError_t e);           // records the error, returns SR_
 const DeviceInfo* current_device(int* status);  // cached per device
 int get_workspace(cudaStream_t s, Workspace* ws);
 void release_workspace(cudaStream_t s);  // frees the workspace of (current device, s)
+void release_host_pipe(cudaStream_t s);  // frees the host-entry staging of (current device, s)
 uint64_t spin_limit_ns();
 
 // Cached per-function launch facts (one query per function and shape).

@@ -34,3 +34,25 @@ def test_bounded_wait_times_out_and_context_survives(sr):
 def test_selftest_rejects_bad_limits(sr):
     assert sr.selftest_bounded_wait(0) == sr.ERR_ARG
     assert sr.selftest_bounded_wait(20_000_000_000) == sr.ERR_ARG
+
+
+def test_stream_release_and_reuse(sr):
+    """Workspaces and staging buffers of a stream are freed on request and
+    re-created by the next call on it."""
+    x = workloads.uniform_i32(1 << 20, seed=6)
+    xd = torch.from_numpy(x).cuda()
+    pinned = torch.from_numpy(x).pin_memory()
+    host_out = np.zeros(1, np.int64)
+    for _ in range(3):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            out = sr.reduce_sum(xd, variant=sr.LAST_BLOCK, stream=s)
+        sr.check(sr.reduce_sum_host_ptr(pinned.data_ptr(), x.size, sr.I32, host_out.ctypes.data, None, s))
+        s.synchronize()
+        assert int(out.item()) == int(host_out[0]) == oracle.sum_i32(x)
+        assert sr.stream_release(s) == sr.OK
+        with torch.cuda.stream(s):
+            out = sr.reduce_sum(xd, variant=sr.LAST_BLOCK, stream=s)   # workspace re-created
+        s.synchronize()
+        assert int(out.item()) == oracle.sum_i32(x)
+        assert sr.stream_release(s) == sr.OK
