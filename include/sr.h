@@ -84,6 +84,13 @@ typedef enum {
                                    binary64; `out` is then a double */
 #define SR_F_BULK 0x400         /* load path: TMA bulk copies (cp.async.bulk) into a
                                    shared-memory ring instead of 128/256-bit LDG */
+#define SR_F_FP64_AUTO 0x1000   /* compensated accumulation (implies SR_F_KAHAN) whose
+                                   cross-unit combine switches to binary64 only when the
+                                   binary32 pair combine's error bound (units * 2^-48 *
+                                   sum|unit partials|) could exceed 1e-6 |S|; `out`
+                                   stays binary32.  Ignored under SR_F_FP64_COMBINE.
+                                   Single-array stages with a cross-unit combine
+                                   (two-kernel, last-block, grid-sync); not segmented. */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses
@@ -171,7 +178,9 @@ int sr_stream_status(sr_stream_t stream);
  * staging buffers for (current device, stream); a later call on the stream
  * allocates them again.  Call it before destroying a stream the library
  * was used on (otherwise they live until the process exits).  Pending
- * error flags of the stream are discarded with the workspace. */
+ * error flags of the stream are discarded with the workspace.  A CUDA graph
+ * captured from calls on this stream holds pointers into the freed
+ * workspace: destroy such graphs first. */
 int sr_stream_release(sr_stream_t stream);
 
 /* Resolve the launch shape the library would use for this call on the

@@ -47,7 +47,7 @@ struct DeviceInfo {
 struct Plan {
     int dtype = 0, elem = 4;
     int stage = 0, log2c = 0, cluster = 1;
-    bool comp = false, fp64 = false, bulk = false;
+    bool comp = false, fp64 = false, fp64_auto = false, bulk = false;
     int block = 0, grid = 0, units = 0;
     int vec = 16, unroll = 4;
     int tile = 0, stages = 0;

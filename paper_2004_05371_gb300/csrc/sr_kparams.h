@@ -22,6 +22,7 @@ struct KParams {
     float scale;              // applied once to the final float result
     int stage;                // grid stage (sr_stage)
     int fp64;                 // combine unit partials in binary64
+    int fp64_auto;            // compensated partials: binary64 combine only when needed
     int units;                // number of units (= grid / cluster)
     int log2c;                // cluster size = 1 << log2c
     int tile_bytes;           // bulk path: bytes per stage

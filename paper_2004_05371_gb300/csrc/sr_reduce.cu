@@ -10,7 +10,7 @@ namespace sr {
 namespace {
 
 constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK |
-                            SR_F_HOST_DIRECT;
+                            SR_F_HOST_DIRECT | SR_F_FP64_AUTO;
 // SR_AUTO's launch shapes, from graph-timed size sweeps and autotuner sweeps
 // on a GB300 (device time per call):
 //   <= 16 KiB : one CTA, no grid stage                       (1.8-2.0 us)
@@ -83,8 +83,9 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
     p.dtype = dtype;
     p.elem = elem_size(dtype);
     p.n = n;
-    p.comp = (c.variant & SR_F_KAHAN) && dtype != SR_I32;
+    p.comp = (c.variant & (SR_F_KAHAN | SR_F_FP64_AUTO)) && dtype != SR_I32;
     p.fp64 = (c.variant & SR_F_FP64_COMBINE) && dtype != SR_I32;
+    p.fp64_auto = (c.variant & SR_F_FP64_AUTO) && dtype != SR_I32 && !p.fp64;
     p.bulk = (c.variant & SR_F_BULK) != 0;
     p.scale = (dtype == SR_FP8E4M3 && c.scale != 0.f) ? c.scale : 1.f;
     p.stage = c.variant & SR_STAGE_MASK;
@@ -213,6 +214,7 @@ int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, 
     kp.scale = p.scale;
     kp.stage = p.stage;
     kp.fp64 = p.fp64 ? 1 : 0;
+    kp.fp64_auto = p.fp64_auto ? 1 : 0;
     kp.units = p.units;
     kp.log2c = p.log2c;
     kp.tile_bytes = p.tile;
@@ -290,6 +292,7 @@ int reduce_launch_final(const Plan& p, int units, void* out, const Workspace& ws
     kp.partials = ws.partials;
     kp.scale = p.scale;
     kp.fp64 = p.fp64 ? 1 : 0;
+    kp.fp64_auto = p.fp64_auto ? 1 : 0;
     kp.units = units;
     void* args[] = {&kp};
     const int threads = std::min(1024, std::max(32, ((units + 31) / 32) * 32));

@@ -71,6 +71,41 @@ template <class P> __device__ __forceinline__ void reduce_slots(const KParams& p
     if (threadIdx.x == 0) out_write(v, p);
 }
 
+// Compensated unit partials: the (sum, correction) pairs are combined in
+// binary32 pair arithmetic, whose error is at most about units * u^2 *
+// sum|s_i| (u = 2^-24: each pair addition rounds only its correction terms).
+// With fp64_auto set, when that bound could exceed 1e-6 |S| the block
+// recombines the partials in binary64 (fixed order) before writing the
+// binary32 result — binary64 only in the cross-unit combine, only when the
+// compensated bound is not met.
+template <> __device__ __forceinline__ void reduce_slots<Pair>(const KParams& p) {
+    __shared__ __align__(16) unsigned char scratch_raw[32 * sizeof(double)];
+    __shared__ int s_redo;
+    Pair v = Op<Pair>::zero();
+    float a = 0.f;
+    for (int i = threadIdx.x; i < p.units; i += blockDim.x) {
+        const Pair q = slot_load<Pair>(p.partials + (size_t)i * 16);
+        v = Op<Pair>::add(v, q);
+        a = __fadd_rn(a, fabsf(q.s));
+    }
+    v = block_reduce(v, reinterpret_cast<Pair*>(scratch_raw));
+    a = block_reduce(a, reinterpret_cast<float*>(scratch_raw));
+    if (threadIdx.x == 0) {
+        const double S = fabs((double)to_float(v));
+        s_redo = p.fp64_auto && (double)p.units * 0x1p-48 * (double)a > 1e-6 * S;
+    }
+    __syncthreads();
+    if (!s_redo) {
+        if (threadIdx.x == 0) out_write(v, p);
+        return;
+    }
+    double d = 0.0;
+    for (int i = threadIdx.x; i < p.units; i += blockDim.x)
+        d = __dadd_rn(d, to_double(slot_load<Pair>(p.partials + (size_t)i * 16)));
+    d = block_reduce(d, reinterpret_cast<double*>(scratch_raw));
+    if (threadIdx.x == 0) *reinterpret_cast<float*>(p.out) = __double2float_rn(__dmul_rn(d, (double)p.scale));
+}
+
 template <class A> __device__ __forceinline__ void reduce_slots_any(const KParams& p) {
     if (p.fp64) reduce_slots<double>(p);
     else reduce_slots<A>(p);

@@ -30,8 +30,8 @@ int seg_validate(const void* x, const int64_t* offsets, int64_t nseg, int dtype,
     if (offsets && reinterpret_cast<uintptr_t>(offsets) % 8) return SR_ERR_ARG;
     const bool fp64 = (c.variant & SR_F_FP64_COMBINE) && dtype != SR_I32;
     if (out && reinterpret_cast<uintptr_t>(out) % ((dtype == SR_I32 || fp64) ? 8 : 4)) return SR_ERR_ARG;
-    if (c.variant & ~kKnownSegFlags) return (c.variant & (SR_F_BULK | SR_CLUSTER_MASK)) ? SR_ERR_UNSUPPORTED
-                                                                                           : SR_ERR_ARG;
+    if (c.variant & ~kKnownSegFlags)
+        return (c.variant & (SR_F_BULK | SR_CLUSTER_MASK | SR_F_FP64_AUTO)) ? SR_ERR_UNSUPPORTED : SR_ERR_ARG;
     const int stage = c.variant & SR_STAGE_MASK;
     if (stage > SR_SINGLE_CLUSTER) return SR_ERR_ARG;
     if (stage == SR_SINGLE_CLUSTER) return SR_ERR_UNSUPPORTED;

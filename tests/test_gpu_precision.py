@@ -158,3 +158,23 @@ def test_full_size_precision_workloads(sr):
     S = oracle.to_float(oracle.exact_f32(xc))
     got = _run(sr, _dev(xc), sr.AUTO | sr.F_KAHAN | sr.F_FP64_COMBINE)
     assert abs(got - S) / abs(S) <= 1e-6, (got, S)
+
+
+def test_fp64_auto_combine(sr):
+    """SR_F_FP64_AUTO: binary64 only in the cross-unit combine and only when the
+    pair combine's bound is not met — identical to the compensated result on
+    well-conditioned data, within 1e-6 relative on cond ~1e8 data."""
+    x = np.abs(workloads.lognormal_f32((1 << 22) + 3, seed=7, sigma=1.0))
+    xd = _dev(x)
+    for stage in (sr.TWO_KERNEL, sr.LAST_BLOCK, sr.GRID_SYNC):
+        a = _run(sr, xd, stage | sr.F_KAHAN)
+        b = _run(sr, xd, stage | sr.F_FP64_AUTO)
+        assert a == b
+    n = 1 << 22
+    xc = workloads.cancelling_f32(n, cond=1e8, seed=0)
+    S = oracle.to_float(oracle.exact_f32(xc))
+    xd = _dev(xc)
+    for stage in (sr.TWO_KERNEL, sr.LAST_BLOCK, sr.GRID_SYNC):
+        out = sr.reduce_sum(xd, variant=stage | sr.F_FP64_AUTO)
+        assert out.dtype == torch.float32
+        assert abs(float(out.item()) - S) / abs(S) <= 1e-6
