@@ -13,8 +13,9 @@ constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_
                             SR_F_HOST_DIRECT | SR_F_FP64_AUTO;
 // SR_AUTO's launch shapes, from graph-timed size sweeps and autotuner sweeps
 // on a GB300 (device time per call):
-//   <= 16 KiB : one CTA, no grid stage                       (1.8-2.0 us)
-//   <= 1 MiB  : one cluster of 8 CTAs, DSMEM merge, no grid stage (2.2-3.0 us)
+//   <= 16 KiB : one CTA of 256 threads, 32 B x 2 loads, no grid stage (1.76 us at 16 KiB)
+//   <= 1 MiB  : one cluster of 16 such CTAs, DSMEM merge, no grid stage
+//               (1.98 us at 64 KiB, 2.10 at 256 KiB, 2.44 at 1 MiB)
 //   <= 64 MiB : two-kernel form, grid sized by the work      (3.5-15 us)
 //   larger    : last-block-done with the per-dtype shape below (HBM-bound)
 struct AutoShape {
@@ -97,7 +98,10 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
         const bool chosen_cluster = p.log2c != 0;
         if (bytes <= kAutoClusterBytes) {
             p.stage = SR_SINGLE_CLUSTER;
-            if (!chosen_cluster) p.log2c = bytes <= kAutoOneCtaBytes ? 0 : 3;
+            if (!chosen_cluster) p.log2c = bytes <= kAutoOneCtaBytes ? 0 : 4;
+            def_block = 256;
+            def_vec = 32;
+            def_unroll = 2;
         } else if (bytes <= kAutoTwoKernelBytes) {
             p.stage = SR_TWO_KERNEL;
         } else {
