@@ -306,8 +306,10 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int s = (int)(k % S);
             const uint32_t ph = (uint32_t)((k / S) & 1);
-            if (!mbar_wait_bounded(full0 + 8u * s, ph, p.limit_ns)) {
-                atomicOr(p.err, kErrTimeout);
+            // one decision per warp: every lane leaves, or none does, so the
+            // __syncwarp and the shuffles below always see the whole warp
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(full0 + 8u * s, ph, p.limit_ns))) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
                 break;
             }
             const int64_t t = (int64_t)blockIdx.x + k * gridDim.x;
