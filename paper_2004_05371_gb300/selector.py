@@ -131,8 +131,10 @@ def train(X, Q, hidden=64, steps=3000, batch=256, lr=3e-3, seed=0, device="cuda"
 
 
 def default_model_params(sms):
-    """Performance-model parameters for a GB300 (measured with
-    sr_barrier_bench and the single-array reduction)."""
+    """Performance-model parameters for a GB300: HBM throughput of the
+    single-array reduction at 2^28 elements, kernel-boundary overhead (Eq. 6)
+    and grid.sync cost measured with sr_barrier_bench; latency and the
+    per-CTA / per-segment terms fitted to autotuner timings."""
     return ModelParams(sms=sms, hbm_bytes_per_ns=6900.0, mem_latency_ns=900.0, launch_ns=2250.0,
                        grid_sync_ns=1150.0, last_block_ns=800.0, atomic_ns=400.0, per_cta_ns=4.0,
                        per_segment_ns=150.0)
