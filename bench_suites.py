@@ -56,6 +56,8 @@ def selector_suite(args):
     ch = sel.choose(Xte)
     r_mlp = selector.regret(Tte, ch)
     r_model = selector.regret(Tte, selector.analytic_choices(te, cands, selector.default_model_params(sms)))
+    fitted, train_regret = selector.fit_model_params(tr, Ttr, cands, sms)
+    r_fit = selector.regret(Tte, selector.analytic_choices(te, cands, fitted))
     # a fixed default: last-block, full grid (8 CTAs/SM), 16-byte vectors
     fixed = [i for i, c in enumerate(cands) if c.variant == sr.LAST_BLOCK and c.grid == 8 * sms and
              c.vec_bytes == 16][0]
@@ -73,7 +75,9 @@ def selector_suite(args):
     _emit({"suite": "selector", "train_shapes": len(tr), "train_timings": int(np.isfinite(Ttr).sum()),
            "heldout_shapes": len(te), "candidates": len(cands), "collect_s": round(t_collect, 1),
            "train_s": round(t_train, 1), "final_loss": losses[-1][1], "regret_mlp": summ(r_mlp),
-           "regret_model": summ(r_model), "regret_fixed_default": summ(r_fixed),
+           "regret_model": summ(r_model), "regret_model_fitted": summ(r_fit),
+           "model_fitted_params": {f: round(getattr(fitted, f), 3) for f in selector.FIT_FIELDS},
+           "regret_fixed_default": summ(r_fixed),
            "mlp_inference_us_per_call": round(infer_us, 2)})
     return 0
 

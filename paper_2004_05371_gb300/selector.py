@@ -133,8 +133,9 @@ def train(X, Q, hidden=64, steps=3000, batch=256, lr=3e-3, seed=0, device="cuda"
 def default_model_params(sms):
     """Performance-model parameters for a GB300: HBM throughput of the
     single-array reduction at 2^28 elements, kernel-boundary overhead (Eq. 6)
-    and grid.sync cost measured with sr_barrier_bench; latency and the
-    per-CTA / per-segment terms fitted to autotuner timings."""
+    and grid.sync cost measured with sr_barrier_bench; memory latency and the
+    last-block, atomic, per-CTA and per-segment terms are hand-set starting
+    values (see fit_model_params)."""
     return ModelParams(sms=sms, hbm_bytes_per_ns=6900.0, mem_latency_ns=900.0, launch_ns=2250.0,
                        grid_sync_ns=1150.0, last_block_ns=800.0, atomic_ns=400.0, per_cta_ns=4.0,
                        per_segment_ns=150.0)
@@ -143,3 +144,35 @@ def default_model_params(sms):
 def analytic_choices(shapes, cands, params):
     return np.array([select_analytic(params, s["n"], s["dtype"], s["nseg"], cands)[0] for s in shapes],
                     dtype=np.int64)
+
+
+FIT_FIELDS = ("hbm_bytes_per_ns", "mem_latency_ns", "launch_ns", "grid_sync_ns", "last_block_ns", "atomic_ns",
+              "per_cta_ns", "per_segment_ns")
+
+
+def fit_model_params(shapes, T, cands, sms, rounds=4, seed=0):
+    """Calibrate the performance model on training timings: coordinate
+    descent over log-scaled multipliers of each parameter, minimising the
+    mean regret of the model's choices on the training shapes.  Gives the
+    method without the network its best shot before the comparison."""
+    p = default_model_params(sms)
+
+    def score(params):
+        ch = analytic_choices(shapes, cands, params)
+        return float(np.mean(regret(T, ch)))
+
+    best = score(p)
+    factors = (0.25, 0.5, 0.8, 1.25, 2.0, 4.0)
+    for _ in range(rounds):
+        improved = False
+        for f in FIT_FIELDS:
+            base = getattr(p, f)
+            for m in factors:
+                setattr(p, f, base * m)
+                sc = score(p)
+                if sc < best - 1e-6:
+                    best, base, improved = sc, base * m, True
+            setattr(p, f, base)
+        if not improved:
+            break
+    return p, best
