@@ -228,6 +228,14 @@ def sweep_suite(args):
                        "warm_us": round(warm * 1e3, 2), "cold_us": round(cold * 1e3, 2),
                        "warm_gbs": round(n * 4 / (warm * 1e-3) / 1e9, 1),
                        "cold_gbs": round(n * 4 / (cold * 1e-3) / 1e9, 1)})
+            # library reference point (not on the path): PyTorch's own reduction kernel
+            if dt == "f32":
+                try:
+                    warm = graph_time(lambda: torch.sum(x), calls)
+                    _emit({"suite": "sweep", "dtype": dt, "log2n": k, "variant": "torch.sum (library reference)",
+                           "warm_us": round(warm * 1e3, 2), "warm_gbs": round(n * 4 / (warm * 1e-3) / 1e9, 1)})
+                except Exception as e:
+                    _emit({"suite": "sweep", "dtype": dt, "log2n": k, "variant": "torch.sum", "error": str(e)[:120]})
     return 0
 
 
