@@ -1,0 +1,68 @@
+"""The autotuner, the planner's SR_AUTO regimes and the performance-model
+selector on the device."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_plan_auto_regimes(sr):
+    """SR_AUTO: one CTA up to 16 KiB, a 16-CTA cluster up to 1 MiB, the
+    two-kernel form up to 64 MiB, then last-block-done (FP32 sizes)."""
+    cases = [(1 << 10, sr.SINGLE_CLUSTER, 0), (1 << 12, sr.SINGLE_CLUSTER, 0), (1 << 14, sr.SINGLE_CLUSTER, 4),
+             (1 << 18, sr.SINGLE_CLUSTER, 4), (1 << 20, sr.TWO_KERNEL, 0), (1 << 24, sr.TWO_KERNEL, 0),
+             (1 << 26, sr.LAST_BLOCK, 0), (1 << 28, sr.LAST_BLOCK, 0)]
+    for n, stage, log2c in cases:
+        r = sr.plan(n, sr.F32)
+        assert r.variant & sr.STAGE_MASK == stage, n
+        assert (r.variant & sr.CLUSTER_MASK) >> sr.CLUSTER_SHIFT == log2c, n
+    r = sr.plan(1 << 28, sr.F32)
+    assert (r.vec_bytes, r.unroll, r.block_threads) == (32, 8, 512)
+    r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.F_KAHAN))
+    assert r.variant & sr.F_BULK and r.tile_bytes == 32768 and r.stages == 4
+    # explicit fields override the table
+    r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.AUTO, vec_bytes=16, unroll=2))
+    assert (r.vec_bytes, r.unroll) == (16, 2)
+
+
+def test_autotune_times_every_candidate(sr):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 1 << 24
+    x = torch.from_numpy(workloads.uniform_f32(n, seed=1)).cuda()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cands = sr.candidates(sms)
+    us = sr.autotune(x.data_ptr(), n, sr.F32, out.data_ptr(), cands, reps=2)
+    assert len(us) == len(cands)
+    finite = [u for u in us if math.isfinite(u)]
+    assert len(finite) >= 30 and all(0 < u < 10_000 for u in finite)
+    # candidates that cannot run are marked, not fatal: a grid.sync grid larger
+    # than what can be co-resident
+    bad = (sr.Config * 1)(sr.make_config(sr.GRID_SYNC, grid=sms * 64, block_threads=1024))
+    assert math.isinf(sr.autotune(x.data_ptr(), n, sr.F32, out.data_ptr(), bad, reps=1)[0])
+    # segmented form
+    off = workloads.segment_offsets(1000, n, seed=2, median=4096, sigma=1.5, hi=1 << 22)
+    od = torch.from_numpy(off).cuda()
+    outs = torch.zeros(1000, dtype=torch.float64, device="cuda")
+    us = sr.autotune(x.data_ptr(), int(off[-1]), sr.F32, outs.data_ptr(), cands, reps=2,
+                     offsets_ptr=od.data_ptr(), nseg=1000)
+    assert sum(math.isfinite(u) for u in us) >= 30
+
+
+def test_model_selector_picks_a_reasonable_candidate(sr):
+    """The performance model's choice is within 50 % of the best measured
+    candidate at a large and a small size (it is the baseline, not the goal)."""
+    from paper_2004_05371_gb300 import selector
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cands = sr.candidates(sms)
+    params = selector.default_model_params(sms)
+    for n in (1 << 26, 1 << 14):
+        x = torch.from_numpy(workloads.uniform_f32(n, seed=3)).cuda()
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        us = np.array(sr.autotune(x.data_ptr(), n, sr.F32, out.data_ptr(), cands, reps=3))
+        i, pred = sr.select_analytic(params, n, sr.F32, 1, cands)
+        assert np.isfinite(us[i]) and us[i] <= 1.5 * np.min(us), (n, us[i], np.min(us))
