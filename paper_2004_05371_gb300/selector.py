@@ -136,8 +136,10 @@ def default_model_params(sms):
     and grid.sync cost measured with sr_barrier_bench; memory latency and the
     last-block, atomic, per-CTA and per-segment terms are hand-set starting
     values (see fit_model_params)."""
+    # atomic_ns includes the memset node that zeroes `out` before an atomic finish;
+    # last_block_ns the __threadfence + ticket + final reduction of the last unit
     return ModelParams(sms=sms, hbm_bytes_per_ns=6900.0, mem_latency_ns=900.0, launch_ns=2250.0,
-                       grid_sync_ns=1150.0, last_block_ns=800.0, atomic_ns=400.0, per_cta_ns=4.0,
+                       grid_sync_ns=1150.0, last_block_ns=1500.0, atomic_ns=2500.0, per_cta_ns=4.0,
                        per_segment_ns=150.0)
 
 
