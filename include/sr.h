@@ -185,7 +185,8 @@ int sr_stream_release(sr_stream_t stream);
 
 /* Resolve the launch shape the library would use for this call on the
  * current device, without launching: fills *resolved (variant with the
- * stage chosen, block_threads, grid, vec_bytes, unroll, tile_bytes, stages).
+ * stage, cluster and load path chosen, block_threads, grid, vec_bytes,
+ * unroll, tile_bytes, stages).
  * Needs a device; returns the same errors sr_reduce_sum_ex would. */
 int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
 

@@ -343,7 +343,8 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved) {
     st = reduce_plan(fake, n, dtype, c, *d, &p);
     if (st != SR_OK) return st;
     sr_config r = c;
-    r.variant = (c.variant & ~(SR_STAGE_MASK | SR_CLUSTER_MASK)) | p.stage | SR_CLUSTER(p.log2c);
+    r.variant = (c.variant & ~(SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_BULK)) | p.stage | SR_CLUSTER(p.log2c) |
+                (p.bulk ? SR_F_BULK : 0) | (p.comp ? SR_F_KAHAN : 0);
     r.block_threads = p.block;
     r.grid = p.grid;
     r.vec_bytes = p.vec;
