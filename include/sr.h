@@ -312,9 +312,14 @@ typedef struct {
  * throughput Thr = min(peak, bytes in flight / T) (Eq. 1 read as the
  * concurrency a launch shape sustains), C = T * Thr, and predicted time
  * launch + T + T_sync(stage) + max(0, N - C) / Thr (Eqs. 2-3) plus the
- * per-CTA and per-segment terms; N = n * sizeof(dtype).  Writes the
- * predictions (microseconds) to predicted_us when non-NULL and returns the
- * index of the cheapest candidate (or -sr_status).  Host only. */
+ * per-CTA and per-segment terms; N = n * sizeof(dtype).  A candidate that
+ * sr_plan (nseg == 1) or sr_plan_segmented (nseg > 1) rejects on the current
+ * device with SR_ERR_LAUNCH / SR_ERR_UNSUPPORTED / SR_ERR_ARG (for instance a
+ * grid.sync() grid larger than the co-resident CTAs, Section VIII-B) is never
+ * chosen and is predicted +infinity; with no device visible the planner is not
+ * consulted.  Writes the predictions (microseconds) to predicted_us when
+ * non-NULL and returns the index of the cheapest candidate, -SR_ERR_LAUNCH if
+ * every candidate is rejected, or -SR_ERR_ARG.  Launches nothing. */
 int sr_select_analytic(const sr_model_params* params, int64_t n, int dtype, int64_t nseg, const sr_config* cands,
                        int ncand, float* predicted_us);
 

@@ -128,7 +128,17 @@ int sr_selector_features(int64_t n, int dtype, int64_t nseg, double len_mean, do
     return SR_OK;
 }
 
-// Performance-model selector (host only).
+// A candidate the planner rejects on the current device (a grid.sync() grid
+// that cannot be co-resident, Section VIII-B; a shape the kernels do not
+// cover) can never run, so the model never chooses it.  With no device
+// visible the planner cannot answer and every candidate stays eligible.
+static bool rejected_by_planner(const sr_config& c, int64_t n, int dtype, int64_t nseg) {
+    sr_config r;
+    const int st = nseg > 1 ? sr_plan_segmented(nseg, dtype, &c, &r) : sr_plan(n, dtype, &c, &r);
+    return st == SR_ERR_LAUNCH || st == SR_ERR_UNSUPPORTED || st == SR_ERR_ARG;
+}
+
+// Performance-model selector (host only: it launches nothing).
 int sr_select_analytic(const sr_model_params* mp, int64_t n, int dtype, int64_t nseg, const sr_config* cands,
                        int ncand, float* predicted_us) {
     if (!mp || !cands || ncand <= 0 || n < 0 || nseg < 1 || dtype < SR_F32 || dtype > SR_FP8E4M3) return -SR_ERR_ARG;
@@ -137,6 +147,10 @@ int sr_select_analytic(const sr_model_params* mp, int64_t n, int dtype, int64_t 
     double best_t = INFINITY;
     for (int i = 0; i < ncand; ++i) {
         const sr_config& c = cands[i];
+        if (rejected_by_planner(c, n, dtype, nseg)) {
+            if (predicted_us) predicted_us[i] = INFINITY;
+            continue;
+        }
         const int stage = c.variant & SR_STAGE_MASK;
         const double warps = (double)(c.grid > 0 ? c.grid : mp->sms) * (c.block_threads > 0 ? c.block_threads : 256) / 32.0;
         const double per_warp_bytes = 32.0 * (c.vec_bytes > 0 ? c.vec_bytes : 16) * (c.unroll > 0 ? c.unroll : 4);
@@ -159,7 +173,7 @@ int sr_select_analytic(const sr_model_params* mp, int64_t n, int dtype, int64_t 
             best = i;
         }
     }
-    return best;
+    return best >= 0 ? best : -SR_ERR_LAUNCH;
 }
 
 }  // extern "C"

@@ -114,7 +114,7 @@ def test_learned_selector_beats_the_model_without_it(sr):
     fitted, _ = selector.fit_model_params(tr, Ttr, cands, sms)
     r_fit = selector.regret(Tte, selector.analytic_choices(te, cands, fitted))
     print("mean regret: mlp %.4f  model %.4f  model fitted %.4f" % (r_mlp.mean(), r_model.mean(), r_fit.mean()))
-    assert np.all(np.isfinite(r_mlp))
+    assert np.all(np.isfinite(r_mlp)) and np.all(np.isfinite(r_model)) and np.all(np.isfinite(r_fit))
     assert r_mlp.mean() < min(r_model.mean(), r_fit.mean())
 
 

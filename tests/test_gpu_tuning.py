@@ -66,3 +66,31 @@ def test_model_selector_picks_a_reasonable_candidate(sr):
         us = np.array(sr.autotune(x.data_ptr(), n, sr.F32, out.data_ptr(), cands, reps=3))
         i, pred = sr.select_analytic(params, n, sr.F32, 1, cands)
         assert np.isfinite(us[i]) and us[i] <= 2.0 * np.min(us), (n, us[i], np.min(us))
+
+
+def test_model_selector_never_picks_a_rejected_launch(sr):
+    """A grid.sync() candidate whose grid cannot be co-resident is rejected by
+    the planner (Section VIII-B), so the model never chooses it — even when
+    its formula alone would rank it first — and predicts +inf for it; the
+    same holds for the segmented planner."""
+    from paper_2004_05371_gb300 import selector
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    params = selector.default_model_params(sms)
+    params.grid_sync_ns = 0.0                   # makes grid.sync the model's favourite
+    too_big = sr.make_config(sr.GRID_SYNC, grid=64 * sms, block_threads=1024, vec_bytes=32, unroll=8)
+    fits = sr.make_config(sr.LAST_BLOCK, grid=sms, block_threads=256, vec_bytes=16, unroll=1)
+    cands = (sr.Config * 2)(too_big, fits)
+    for nseg in (1, 1000):
+        i, pred = sr.select_analytic(params, 1 << 26, sr.F32, nseg, cands)
+        assert i == 1 and math.isinf(pred[0]) and math.isfinite(pred[1]), nseg
+    with pytest.raises(sr.SRError):
+        sr.select_analytic(params, 1 << 26, sr.F32, 1, (sr.Config * 1)(too_big))
+    # every choice over the standard candidate set is a launch the planner accepts
+    cands = sr.candidates(sms)
+    for n in (1 << 12, 1 << 20, 1 << 28):
+        for nseg in (1, 10, 10_000):
+            i, _ = sr.select_analytic(params, n, sr.F32, nseg, cands)
+            if nseg > 1:
+                sr.plan_segmented(nseg, sr.F32, cands[i])
+            else:
+                sr.plan(n, sr.F32, cands[i])
