@@ -149,11 +149,12 @@ def precision_suite(args):
             xd = torch.from_numpy(arr).cuda()
         S = oracle.to_float(exact)
         cond = sabs / abs(S) if S else float("inf")
-        for mode, flags in (("plain", 0), ("kahan", sr.F_KAHAN), ("kahan+fp64", sr.F_KAHAN | sr.F_FP64_COMBINE)):
+        for mode, flags in (("plain", 0), ("kahan", sr.F_KAHAN), ("kahan+fp64", sr.F_KAHAN | sr.F_FP64_COMBINE),
+                            ("kahan+fp64_auto", sr.F_FP64_AUTO)):
             cfg = sr.make_config(sr.AUTO | flags, scale=scale or 0.0)  # last-block-done at this size
             out = sr.reduce_sum(xd, config=cfg)
             got = float(out.item())
-            ms = _time_calls(torch, lambda: sr.reduce_sum(xd, config=cfg, out=out), 10, st)
+            ms = _time_calls(torch, lambda: sr.reduce_sum(xd, config=cfg, out=out), 30, st)
             _emit({"suite": "precision", "input": name, "dtype": dt, "mode": mode, "n": n,
                    "cond": cond, "exact": S, "fp64_oracle": s64, "gpu": got,
                    "abs_err": abs(got - S), "rel_err": abs(got - S) / abs(S) if S else None,
