@@ -111,8 +111,15 @@ def barrier_suite(args):
         for t in (32, 128, 256, 512, 1024):
             if per_sm * t <= 2048:
                 run(sr.LEVEL_GRID, blocks=per_sm * sms, threads=t, iters=20000)
-    run(sr.LEVEL_KERNEL, reps=20)
+    for kind in (sr.LAUNCH_TRADITIONAL, sr.LAUNCH_COOPERATIVE, sr.LAUNCH_CLUSTER):   # Table I
+        run(sr.LEVEL_KERNEL, reps=20, method=kind)
+    run(sr.LEVEL_KERNEL, reps=20, method=sr.LAUNCH_COOPERATIVE, blocks=sms)
+    run(sr.LEVEL_KERNEL, reps=20, method=sr.LAUNCH_CLUSTER, cluster=16, blocks=16)
     run(sr.LEVEL_FADD, iters=1_000_000)
+    for fp32 in (0, sr.WR_FP32):                                                     # Table V
+        for m in range(7):
+            run(sr.LEVEL_WARP_REDUCE, method=m | fp32, iters=20000)
+            run(sr.LEVEL_WARP_REDUCE, method=m | fp32, iters=20000, threads=1024)
     return 0
 
 

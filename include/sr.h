@@ -119,9 +119,37 @@ typedef enum {
     SR_LEVEL_KERNEL = 5,     /* implicit kernel-boundary barrier: launch overhead by
                                 the kernel-fusion method (Eq. 6) */
     SR_LEVEL_SHUFFLE = 6,    /* dependent __shfl_xor_sync chain (Table II "Shuffle") */
-    SR_LEVEL_FADD = 7        /* dependent FP32 add chain: the methods' self-check
+    SR_LEVEL_FADD = 7,       /* dependent FP32 add chain: the methods' self-check
                                 (Section IX-D; 4 cycles on V100, 6 on P100) */
+    SR_LEVEL_WARP_REDUCE = 8 /* one warp sums 32 FP64 (or, with SR_WR_FP32, binary32)
+                                values by sr_warp_reduce_method (Table V); one "sync"
+                                = one whole reduction */
 } sr_level;
+
+/* How a warp sums 32 values for SR_LEVEL_WARP_REDUCE (the columns of Table V).
+ * The shared-memory trees halve the active lanes (16, 8, 4, 2, 1) with the
+ * named synchronisation between steps; the shuffle forms use the group's
+ * shfl_down. */
+typedef enum {
+    SR_WR_SERIAL = 0,            /* lane 0 adds the 32 shared-memory values in order */
+    SR_WR_NOSYNC = 1,            /* shared-memory tree, no synchronisation (racy: the
+                                    paper reports its result as incorrect) */
+    SR_WR_VOLATILE_TILE = 2,     /* volatile shared-memory tree + tile(32).sync() */
+    SR_WR_TILE = 3,              /* shared-memory tree + tile(32).sync() */
+    SR_WR_COALESCED = 4,         /* shared-memory tree + coalesced_group.sync() */
+    SR_WR_TILE_SHUFFLE = 5,      /* tile(32).shfl_down tree */
+    SR_WR_COALESCED_SHUFFLE = 6, /* coalesced_group.shfl_down tree */
+    SR_WR_FP32 = 16              /* flag: binary32 values instead of Table V's FP64 */
+} sr_warp_reduce_method;
+
+/* Launch function measured by SR_LEVEL_KERNEL (Table I's rows; the paper's
+ * multi-device cooperative launch no longer exists in CUDA 12+, and the
+ * thread-block-cluster launch of sm_90+ takes its place). */
+typedef enum {
+    SR_LAUNCH_TRADITIONAL = 0,  /* cudaLaunchKernel, the <<<>>> launch */
+    SR_LAUNCH_COOPERATIVE = 1,  /* cudaLaunchCooperativeKernel */
+    SR_LAUNCH_CLUSTER = 2       /* cudaLaunchKernelEx with a cluster-dimension attribute */
+} sr_launch_kind;
 
 /* Launch configuration.  Zero in any field means "library default". */
 typedef struct {
@@ -240,9 +268,13 @@ typedef struct {
     int blocks;     /* CTAs (default: 1; cluster size for SR_LEVEL_CLUSTER; SMs for SR_LEVEL_GRID) */
     int threads;    /* threads per CTA (default: 32 for warp-level levels, 1024 block and
                        cluster, 256 grid) */
-    int cluster;    /* CTAs per cluster, power of two <= 16 (SR_LEVEL_CLUSTER; default 2) */
+    int cluster;    /* CTAs per cluster, power of two <= 16 (SR_LEVEL_CLUSTER and
+                       SR_LAUNCH_CLUSTER: default 2; 0 or 1 elsewhere) */
     int group;      /* tile size (power of two) or coalesced-group size, 1..32 (default 32) */
     int reps;       /* N runs per repeat count for Eqs. 7-8 (default 10) */
+    int method;     /* SR_LEVEL_WARP_REDUCE: sr_warp_reduce_method; SR_LEVEL_KERNEL:
+                       sr_launch_kind (CTAs of 32 threads; `blocks` per launch, default 1,
+                       the cluster size for SR_LAUNCH_CLUSTER); 0 elsewhere */
 } sr_barrier_config;
 
 typedef struct {
@@ -254,6 +286,9 @@ typedef struct {
     double clock_mhz;              /* SM clock seen by the run (clock64 / %globaltimer) */
     double null_kernel_total_ns;   /* SR_LEVEL_KERNEL: null-kernel total latency */
     int blocks, threads;           /* the shape measured */
+    int correct;                   /* SR_LEVEL_WARP_REDUCE: 1 if every reduction of the
+                                      clock64 run produced the exact sum (528), else 0;
+                                      -1 for the other levels */
 } sr_barrier_result;
 
 /* Measure `level` with `iters` back-to-back syncs and default shape; the
@@ -262,8 +297,8 @@ typedef struct {
  * A grid-level shape that cannot be co-resident, or a cluster shape that
  * cannot be scheduled, returns SR_ERR_LAUNCH without launching (a partial
  * grid would wait forever: Section VIII-B).
- * Errors: SR_ERR_ARG (unknown level, iters < 10, bad shape), SR_ERR_LAUNCH,
- * SR_ERR_CUDA. */
+ * Errors: SR_ERR_ARG (unknown level or method, iters < 10, bad shape),
+ * SR_ERR_LAUNCH, SR_ERR_CUDA. */
 int sr_barrier_bench(int level, int64_t iters);
 int sr_barrier_bench_ex(const sr_barrier_config* cfg, sr_barrier_result* result);
 int sr_barrier_bench_last(sr_barrier_result* result);

@@ -28,7 +28,13 @@ F_FP64_AUTO = 0x1000
 # status codes (sr_status)
 OK, ERR_ARG, ERR_DTYPE, ERR_LAUNCH, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 # barrier levels (sr_level)
-LEVEL_WARP, LEVEL_COALESCED, LEVEL_BLOCK, LEVEL_CLUSTER, LEVEL_GRID, LEVEL_KERNEL, LEVEL_SHUFFLE, LEVEL_FADD = range(8)
+(LEVEL_WARP, LEVEL_COALESCED, LEVEL_BLOCK, LEVEL_CLUSTER, LEVEL_GRID, LEVEL_KERNEL, LEVEL_SHUFFLE, LEVEL_FADD,
+ LEVEL_WARP_REDUCE) = range(9)
+# sr_warp_reduce_method (Table V) and sr_launch_kind (Table I)
+(WR_SERIAL, WR_NOSYNC, WR_VOLATILE_TILE, WR_TILE, WR_COALESCED, WR_TILE_SHUFFLE,
+ WR_COALESCED_SHUFFLE) = range(7)
+WR_FP32 = 16
+LAUNCH_TRADITIONAL, LAUNCH_COOPERATIVE, LAUNCH_CLUSTER = range(3)
 
 
 def CLUSTER(log2c: int) -> int:
@@ -50,7 +56,7 @@ class BarrierConfig(ctypes.Structure):
     """Mirror of ``sr_barrier_config``."""
     _fields_ = [("level", ctypes.c_int), ("iters", ctypes.c_int64), ("blocks", ctypes.c_int),
                 ("threads", ctypes.c_int), ("cluster", ctypes.c_int), ("group", ctypes.c_int),
-                ("reps", ctypes.c_int)]
+                ("reps", ctypes.c_int), ("method", ctypes.c_int)]
 
 
 class BarrierResult(ctypes.Structure):
@@ -58,7 +64,7 @@ class BarrierResult(ctypes.Structure):
     _fields_ = [("cycles_per_sync", ctypes.c_double), ("ns_per_sync", ctypes.c_double),
                 ("ns_sigma", ctypes.c_double), ("syncs_per_cycle_per_sm", ctypes.c_double),
                 ("clock_mhz", ctypes.c_double), ("null_kernel_total_ns", ctypes.c_double),
-                ("blocks", ctypes.c_int), ("threads", ctypes.c_int)]
+                ("blocks", ctypes.c_int), ("threads", ctypes.c_int), ("correct", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -336,9 +342,9 @@ class SegmentedGraph:
 
 
 def barrier_bench(level: int, iters: int = 0, blocks: int = 0, threads: int = 0, cluster: int = 0,
-                  group: int = 0, reps: int = 0) -> dict:
+                  group: int = 0, reps: int = 0, method: int = 0) -> dict:
     """sr_barrier_bench_ex: one barrier-latency measurement (raises on error)."""
-    c = BarrierConfig(level, iters, blocks, threads, cluster, group, reps)
+    c = BarrierConfig(level, iters, blocks, threads, cluster, group, reps, method)
     r = BarrierResult()
     check(lib().sr_barrier_bench_ex(ctypes.byref(c), ctypes.byref(r)), "sr_barrier_bench_ex")
     return r.as_dict()

@@ -10,7 +10,10 @@
 //   - the implicit kernel-boundary barrier by kernel fusion (Section IX-B,
 //     Eq. 6): i launches of j wait units against j launches of i wait units
 //     (each unit a nanosleep of 1 us), O = (L_ij - L_ji)/(i - j);
-//   - a dependent FP32 add chain as the methods' self-check (Section IX-D).
+//   - a dependent FP32 add chain as the methods' self-check (Section IX-D);
+//   - the warp-level reductions of Table V: 32 FP64 values summed by one warp
+//     serially, by shared-memory trees under each warp synchronisation, and by
+//     shuffle trees; the result is checked against the exact sum.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,6 +35,7 @@ struct BarParams {
     long long* t;             // per warp: start, end clock64
     unsigned long long* gt;   // block 0 thread 0: globaltimer start, end; clock start, end
     float* sink;
+    unsigned int* bad;        // SR_LEVEL_WARP_REDUCE: reductions that missed the exact sum
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -99,6 +103,92 @@ __global__ void __launch_bounds__(1024) bar_kernel(const BarParams p) {
     if (v == -12345.f) p.sink[0] = v;  // keeps the shuffle / add chains alive
 }
 
+// Table V: every warp sums its lanes' values x = lane + 1 (exact sum 528 in
+// any order, all partial sums small integers) `iters` times by method M, in
+// FP64 as the paper does or in binary32 (T = float).  The next
+// repetition's input depends on this one's result (x0 + 0 unless the result is
+// NaN), so repetitions run one after another, and two shared-memory buffers
+// alternate so that a repetition's stores never overwrite values that a
+// lagging lane of the previous one still reads.
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+template <int M, class T>
+__global__ void __launch_bounds__(1024) warp_reduce_kernel(const BarParams p) {
+    __shared__ T sh[2][32][32];  // [buffer][warp of the CTA][lane]
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const T x0 = (T)(lane + 1);
+    cg::thread_block_tile<32> tile = cg::tiled_partition<32>(cg::this_thread_block());
+    cg::coalesced_group co = cg::coalesced_threads();
+    T s = 0;
+    unsigned int bad = 0;
+    unsigned long long g0 = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) g0 = gtimer();
+    __syncthreads();
+    const long long c0 = clock64();
+    for (int64_t i = 0; i < p.iters; ++i) {
+        const T x = x0 + ((s != s) ? (T)1 : (T)0);
+        T* b = sh[i & 1][wib];
+        if constexpr (M == SR_WR_SERIAL) {
+            b[lane] = x;
+            __syncwarp();
+            if (lane == 0) {
+                T a = 0;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) a = add_rn(a, b[k]);
+                s = a;
+            }
+        } else if constexpr (M == SR_WR_NOSYNC) {
+            b[lane] = x;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+                if (lane < off) b[lane] = add_rn(b[lane], b[lane + off]);
+            s = b[0];
+        } else if constexpr (M == SR_WR_VOLATILE_TILE) {
+            volatile T* v = b;
+            v[lane] = x;
+            tile.sync();
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                if (lane < off) v[lane] = add_rn(v[lane], v[lane + off]);
+                tile.sync();
+            }
+            s = v[0];
+        } else if constexpr (M == SR_WR_TILE || M == SR_WR_COALESCED) {
+            b[lane] = x;
+            if constexpr (M == SR_WR_TILE) tile.sync(); else co.sync();
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                if (lane < off) b[lane] = add_rn(b[lane], b[lane + off]);
+                if constexpr (M == SR_WR_TILE) tile.sync(); else co.sync();
+            }
+            s = b[0];
+        } else if constexpr (M == SR_WR_TILE_SHUFFLE) {
+            s = x;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) s = add_rn(s, tile.shfl_down(s, off));
+        } else {
+            s = x;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) s = add_rn(s, co.shfl_down(s, off));
+        }
+        if (lane == 0) bad += (s != (T)528) ? 1u : 0u;
+    }
+    const long long c1 = clock64();
+    if (lane == 0) {
+        p.t[2 * gw] = c0;
+        p.t[2 * gw + 1] = c1;
+        if (bad) atomicAdd(p.bad, bad);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.gt[0] = g0;
+        p.gt[1] = gtimer();
+        p.gt[2] = (unsigned long long)c0;
+        p.gt[3] = (unsigned long long)c1;
+    }
+}
+
 // One wait unit = a 1 us nanosleep (the paper's null-kernel filler).
 __global__ void sleep_kernel(int units) {
     for (int u = 0; u < units; ++u) __nanosleep(1000);
@@ -117,6 +207,24 @@ const void* bar_fn(int level) {
     }
 }
 
+template <class T> const void* warp_reduce_fn_t(int m) {
+    switch (m) {
+    case SR_WR_SERIAL: return (const void*)warp_reduce_kernel<SR_WR_SERIAL, T>;
+    case SR_WR_NOSYNC: return (const void*)warp_reduce_kernel<SR_WR_NOSYNC, T>;
+    case SR_WR_VOLATILE_TILE: return (const void*)warp_reduce_kernel<SR_WR_VOLATILE_TILE, T>;
+    case SR_WR_TILE: return (const void*)warp_reduce_kernel<SR_WR_TILE, T>;
+    case SR_WR_COALESCED: return (const void*)warp_reduce_kernel<SR_WR_COALESCED, T>;
+    case SR_WR_TILE_SHUFFLE: return (const void*)warp_reduce_kernel<SR_WR_TILE_SHUFFLE, T>;
+    case SR_WR_COALESCED_SHUFFLE: return (const void*)warp_reduce_kernel<SR_WR_COALESCED_SHUFFLE, T>;
+    default: return nullptr;
+    }
+}
+
+const void* warp_reduce_fn(int method) {
+    return (method & SR_WR_FP32) ? warp_reduce_fn_t<float>(method & ~SR_WR_FP32)
+                                 : warp_reduce_fn_t<double>(method);
+}
+
 thread_local sr_barrier_result g_last;
 
 double now_ns() {
@@ -130,10 +238,12 @@ struct Bench {
     long long* t = nullptr;
     unsigned long long* gt = nullptr;
     float* sink = nullptr;
+    unsigned int* bad = nullptr;
     ~Bench() {
         if (t) cudaFree(t);
         if (gt) cudaFree(gt);
         if (sink) cudaFree(sink);
+        if (bad) cudaFree(bad);
         if (s) cudaStreamDestroy(s);
     }
 };
@@ -145,6 +255,7 @@ int launch_bar(const Bench& b, const sr_barrier_config& c, const void* fn, int64
     p.t = b.t;
     p.gt = b.gt;
     p.sink = b.sink;
+    p.bad = b.bad;
     void* args[] = {&p};
     cudaError_t e;
     if (c.level == SR_LEVEL_GRID) {
@@ -190,6 +301,29 @@ void mean_sd(const std::vector<double>& v, double* m, double* sd) {
     *sd = v.size() > 1 ? std::sqrt(q / (v.size() - 1)) : 0.0;
 }
 
+// One launch of the wait-unit kernel by launch function `kind` (Table I).
+cudaError_t launch_sleep(const sr_barrier_config& c, int units, cudaStream_t s) {
+    void* args[] = {&units};
+    if (c.method == SR_LAUNCH_COOPERATIVE)
+        return cudaLaunchCooperativeKernel((const void*)sleep_kernel, dim3(c.blocks), dim3(32), args, 0, s);
+    if (c.method == SR_LAUNCH_CLUSTER) {
+        cudaLaunchConfig_t lc;
+        std::memset(&lc, 0, sizeof lc);
+        lc.gridDim = dim3(c.blocks);
+        lc.blockDim = dim3(32);
+        lc.stream = s;
+        cudaLaunchAttribute a[1];
+        a[0].id = cudaLaunchAttributeClusterDimension;
+        a[0].val.clusterDim.x = c.cluster;
+        a[0].val.clusterDim.y = 1;
+        a[0].val.clusterDim.z = 1;
+        lc.attrs = a;
+        lc.numAttrs = 1;
+        return cudaLaunchKernelExC(&lc, (const void*)sleep_kernel, args);
+    }
+    return cudaLaunchKernel((const void*)sleep_kernel, dim3(c.blocks), dim3(32), args, 0, s);
+}
+
 int kernel_level(const sr_barrier_config& c, sr_barrier_result* r) {
     // Eq. 6 with i = 20 launches of j = 5 units against 5 launches of 20 units,
     // and the null-kernel total latency of Fig. "Sample code to micro-benchmark
@@ -201,8 +335,7 @@ int kernel_level(const sr_barrier_config& c, sr_barrier_result* r) {
     auto run = [&](int launches, int units, double* ns) -> int {
         const double t0 = now_ns();
         for (int k = 0; k < launches; ++k) {
-            void* args[] = {&units};
-            cudaError_t ee = cudaLaunchKernel((const void*)sleep_kernel, dim3(1), dim3(32), args, 0, b.s);
+            cudaError_t ee = launch_sleep(c, units, b.s);
             if (ee != cudaSuccess) return status_from_cuda(ee);
         }
         cudaError_t ee = cudaStreamSynchronize(b.s);
@@ -235,6 +368,9 @@ int kernel_level(const sr_barrier_config& c, sr_barrier_result* r) {
     r->cycles_per_sync = NAN;
     r->syncs_per_cycle_per_sm = NAN;
     r->clock_mhz = NAN;
+    r->blocks = c.blocks;
+    r->threads = 32;
+    r->correct = -1;
     return SR_OK;
 }
 
@@ -248,34 +384,72 @@ extern "C" {
 int sr_barrier_bench_ex(const sr_barrier_config* cfg, sr_barrier_result* out) {
     if (!cfg || !out) return SR_ERR_ARG;
     sr_barrier_config c = *cfg;
-    if (c.level < SR_LEVEL_WARP || c.level > SR_LEVEL_FADD) return SR_ERR_ARG;
+    if (c.level < SR_LEVEL_WARP || c.level > SR_LEVEL_WARP_REDUCE) return SR_ERR_ARG;
+    if (c.level == SR_LEVEL_WARP_REDUCE) {
+        const int m = c.method & ~SR_WR_FP32;
+        if (c.method < 0 || m < SR_WR_SERIAL || m > SR_WR_COALESCED_SHUFFLE) return SR_ERR_ARG;
+    } else if (c.level == SR_LEVEL_KERNEL) {
+        if (c.method < SR_LAUNCH_TRADITIONAL || c.method > SR_LAUNCH_CLUSTER) return SR_ERR_ARG;
+    } else if (c.method != 0) {
+        return SR_ERR_ARG;
+    }
     if (c.iters == 0) c.iters = 100000;
     if (c.reps == 0) c.reps = 10;
     if (c.iters < 10 || c.iters > (int64_t)1 << 32 || c.reps < 2 || c.reps > 1000) return SR_ERR_ARG;
     const bool warp_level = c.level == SR_LEVEL_WARP || c.level == SR_LEVEL_COALESCED ||
-                            c.level == SR_LEVEL_SHUFFLE || c.level == SR_LEVEL_FADD;
+                            c.level == SR_LEVEL_SHUFFLE || c.level == SR_LEVEL_FADD ||
+                            c.level == SR_LEVEL_WARP_REDUCE;
     if (c.threads == 0) c.threads = warp_level ? 32 : (c.level == SR_LEVEL_GRID ? 256 : 1024);
     if (c.threads < 32 || c.threads > 1024 || c.threads % 32) return SR_ERR_ARG;
     if (c.group == 0) c.group = 32;
     if (c.group < 1 || c.group > 32) return SR_ERR_ARG;
     if (c.level == SR_LEVEL_WARP && (c.group & (c.group - 1))) return SR_ERR_ARG;  // tiles are powers of 2
-    if (c.cluster == 0) c.cluster = c.level == SR_LEVEL_CLUSTER ? 2 : 1;
+    const bool cluster_launch = c.level == SR_LEVEL_CLUSTER ||
+                                (c.level == SR_LEVEL_KERNEL && c.method == SR_LAUNCH_CLUSTER);
+    if (c.cluster == 0) c.cluster = cluster_launch ? 2 : 1;
     if (c.cluster < 1 || c.cluster > 16 || (c.cluster & (c.cluster - 1))) return SR_ERR_ARG;
-    if (c.blocks < 0) return SR_ERR_ARG;
+    if (!cluster_launch && c.cluster != 1) return SR_ERR_ARG;
+    if (c.blocks < 0 || (cluster_launch && c.blocks % c.cluster)) return SR_ERR_ARG;
 
     std::memset(out, 0, sizeof *out);
     int st = SR_OK;
     const DeviceInfo* d = current_device(&st);
     if (!d) return st;
-    if (c.blocks == 0) c.blocks = c.level == SR_LEVEL_GRID ? d->sms : (c.level == SR_LEVEL_CLUSTER ? c.cluster : 1);
-    if (c.level == SR_LEVEL_CLUSTER && c.blocks % c.cluster) return SR_ERR_ARG;
+    if (c.blocks == 0) c.blocks = c.level == SR_LEVEL_GRID ? d->sms : (cluster_launch ? c.cluster : 1);
 
     if (c.level == SR_LEVEL_KERNEL) {
+        // never start a cooperative grid that cannot be co-resident, nor a
+        // cluster shape the device cannot schedule
+        const void* sfn = (const void*)sleep_kernel;
+        st = prepare_function(sfn, 0, c.cluster > 8);
+        if (st != SR_OK) return st;
+        if (c.method == SR_LAUNCH_COOPERATIVE) {
+            int per_sm = 0;
+            st = blocks_per_sm(*d, sfn, 32, 0, &per_sm);
+            if (st != SR_OK) return st;
+            if ((int64_t)per_sm * d->sms < c.blocks) return SR_ERR_LAUNCH;
+        } else if (c.method == SR_LAUNCH_CLUSTER) {
+            cudaLaunchConfig_t lc;
+            std::memset(&lc, 0, sizeof lc);
+            lc.gridDim = dim3(c.blocks);
+            lc.blockDim = dim3(32);
+            cudaLaunchAttribute a[1];
+            a[0].id = cudaLaunchAttributeClusterDimension;
+            a[0].val.clusterDim.x = c.cluster;
+            a[0].val.clusterDim.y = 1;
+            a[0].val.clusterDim.z = 1;
+            lc.attrs = a;
+            lc.numAttrs = 1;
+            int nc = 0;
+            st = active_clusters(*d, sfn, &lc, &nc);
+            if (st != SR_OK) return st;
+            if (nc < 1) return SR_ERR_LAUNCH;
+        }
         st = kernel_level(c, out);
         if (st == SR_OK) g_last = *out;
         return st;
     }
-    const void* fn = bar_fn(c.level);
+    const void* fn = c.level == SR_LEVEL_WARP_REDUCE ? warp_reduce_fn(c.method) : bar_fn(c.level);
     st = prepare_function(fn, 0, c.cluster > 8);
     if (st != SR_OK) return st;
     if (c.level == SR_LEVEL_GRID) {
@@ -309,6 +483,7 @@ int sr_barrier_bench_ex(const sr_barrier_config* cfg, sr_barrier_result* out) {
     if ((e = cudaMalloc(&b.t, sizeof(long long) * 2 * nwarps)) != cudaSuccess) return status_from_cuda(e);
     if ((e = cudaMalloc(&b.gt, sizeof(unsigned long long) * 4)) != cudaSuccess) return status_from_cuda(e);
     if ((e = cudaMalloc(&b.sink, sizeof(float))) != cudaSuccess) return status_from_cuda(e);
+    if ((e = cudaMalloc(&b.bad, sizeof(unsigned int))) != cudaSuccess) return status_from_cuda(e);
 
     double w;
     for (int k = 0; k < 2; ++k) {  // warm-up (Section IV: the first launch is not reported)
@@ -326,8 +501,12 @@ int sr_barrier_bench_ex(const sr_barrier_config* cfg, sr_barrier_result* out) {
         L1.push_back(a);
         L2.push_back(bb);
     }
+    if ((e = cudaMemsetAsync(b.bad, 0, sizeof(unsigned int), b.s)) != cudaSuccess) return status_from_cuda(e);
     st = timed_run(b, c, fn, r1, &w);
     if (st != SR_OK) return st;
+    unsigned int nbad = 0;
+    if ((e = cudaMemcpy(&nbad, b.bad, sizeof nbad, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return status_from_cuda(e);
     std::vector<long long> t(2 * nwarps);
     unsigned long long gt[4];
     if ((e = cudaMemcpy(t.data(), b.t, sizeof(long long) * 2 * nwarps, cudaMemcpyDeviceToHost)) != cudaSuccess)
@@ -355,6 +534,7 @@ int sr_barrier_bench_ex(const sr_barrier_config* cfg, sr_barrier_result* out) {
     out->null_kernel_total_ns = NAN;
     out->blocks = c.blocks;
     out->threads = c.threads;
+    out->correct = c.level == SR_LEVEL_WARP_REDUCE ? (nbad == 0 ? 1 : 0) : -1;
     g_last = *out;
     return SR_OK;
 }

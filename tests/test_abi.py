@@ -130,7 +130,45 @@ def test_barrier_bench_rejects_bad_config_without_gpu(lib):
     assert run(level=sr.LEVEL_BLOCK, threads=1000) == sr.ERR_ARG
     assert run(level=sr.LEVEL_CLUSTER, cluster=3) == sr.ERR_ARG
     assert run(level=sr.LEVEL_GRID, reps=1) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_WARP_REDUCE, method=7) == sr.ERR_ARG    # Table V has 7 methods
+    assert run(level=sr.LEVEL_WARP_REDUCE, method=-1) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_WARP_REDUCE, method=sr.WR_FP32 | 7) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_WARP_REDUCE, method=32) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_KERNEL, method=3) == sr.ERR_ARG         # 3 launch functions
+    assert run(level=sr.LEVEL_BLOCK, method=1) == sr.ERR_ARG          # no method elsewhere
+    assert run(level=sr.LEVEL_KERNEL, method=sr.LAUNCH_CLUSTER, cluster=4, blocks=6) == sr.ERR_ARG
+    assert run(level=sr.LEVEL_BLOCK, cluster=2) == sr.ERR_ARG
     assert lib.sr_barrier_bench_ex(None, None) == sr.ERR_ARG
+
+
+def test_structs_match_the_header(tmp_path):
+    """Every ctypes mirror has the layout the C compiler gives the header's
+    struct: a C program built against include/sr.h prints sizeof and the
+    offset of every field, which must equal the binding's."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"sr_config": sr.Config, "sr_barrier_config": sr.BarrierConfig,
+               "sr_barrier_result": sr.BarrierResult, "sr_model_params": sr.ModelParams}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sr.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-x", "c", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                                 text=True).stdout.splitlines())
+    for cname, py in mirrors.items():
+        assert int(got[cname + " size"]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s %s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
 
 
 def test_candidate_set(lib):

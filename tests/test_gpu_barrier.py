@@ -65,3 +65,52 @@ def test_kernel_boundary_overhead(sr):
     last = sr.BarrierResult()
     assert sr.lib().sr_barrier_bench_last(last) == sr.OK
     assert last.cycles_per_sync > 0
+
+
+@pytest.mark.parametrize("fp32", [0, 16])
+@pytest.mark.parametrize("method", [0, 2, 3, 4, 5, 6])
+def test_warp_reduce_methods(sr, method, fp32):
+    """Table V: every synchronised way of summing 32 values in a warp (FP64
+    as in the paper, and binary32) returns the exact sum (528) on every
+    repetition, at one warp and at a full CTA of 32 independent warps."""
+    for threads in (32, 1024):
+        r = sr.barrier_bench(sr.LEVEL_WARP_REDUCE, iters=20000, threads=threads, reps=3, method=method | fp32)
+        assert _ok(r) and 0 < r["cycles_per_sync"] < 200_000, (method, threads, r)
+        assert r["correct"] == 1, (method, fp32, threads)
+
+
+def test_warp_reduce_nosync_runs(sr):
+    """The unsynchronised tree (Table V's "nosync") is measured; its result
+    may be wrong (a data race the paper reports as incorrect), so only the
+    report is checked."""
+    for fp32 in (0, sr.WR_FP32):
+        r = sr.barrier_bench(sr.LEVEL_WARP_REDUCE, iters=20000, reps=3, method=sr.WR_NOSYNC | fp32)
+        assert _ok(r) and r["correct"] in (0, 1)
+
+
+def test_warp_reduce_shuffle_beats_serial(sr):
+    """Table V's ordering at the ends: the tile shuffle tree is faster than one
+    lane adding the 32 values in order."""
+    for fp32 in (0, sr.WR_FP32):
+        ser = sr.barrier_bench(sr.LEVEL_WARP_REDUCE, iters=20000, reps=3, method=sr.WR_SERIAL | fp32)
+        shf = sr.barrier_bench(sr.LEVEL_WARP_REDUCE, iters=20000, reps=3, method=sr.WR_TILE_SHUFFLE | fp32)
+        assert shf["cycles_per_sync"] < ser["cycles_per_sync"], fp32
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_launch_kinds_overhead(sr, kind):
+    """Table I by launch function: traditional, cooperative and cluster
+    launches each give a positive Eq. 6 overhead and null-kernel latency."""
+    r = sr.barrier_bench(sr.LEVEL_KERNEL, reps=5, method=kind)
+    assert 0 < r["ns_per_sync"] < 100_000 and r["null_kernel_total_ns"] > 0, (kind, r)
+    assert r["correct"] == -1
+
+
+def test_launch_kind_guards(sr):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    r = sr.barrier_bench(sr.LEVEL_KERNEL, reps=3, method=sr.LAUNCH_CLUSTER, cluster=16, blocks=32)
+    assert r["blocks"] == 32
+    with pytest.raises(sr.SRError) as e:   # more cooperative CTAs than can be co-resident
+        sr.barrier_bench(sr.LEVEL_KERNEL, reps=2, method=sr.LAUNCH_COOPERATIVE, blocks=sms * 1000)
+    assert e.value.status == sr.ERR_LAUNCH
