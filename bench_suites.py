@@ -182,6 +182,10 @@ def sweep_suite(args):
     import torch
     import paper_2004_05371_gb300 as sr
     sr.load()
+    import libcmp
+    libcmp.build()
+    cmp = libcmp.lib()
+    libcmp.check(cmp.cmp_prepare(1 << 30), "cmp_prepare")
     big = torch.empty(1 << 30, dtype=torch.float32, device="cuda").uniform_(-1, 1)
     bigi = big.view(torch.int32)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -236,6 +240,20 @@ def sweep_suite(args):
                        "warm_us": round(warm * 1e3, 2), "cold_us": round(cold * 1e3, 2),
                        "warm_gbs": round(n * 4 / (warm * 1e-3) / 1e9, 1),
                        "cold_gbs": round(n * 4 / (cold * 1e-3) / 1e9, 1)})
+            # library reference point (not on the path): CUB's DeviceReduce, warm and cold
+            cub_out = torch.empty((), dtype=torch.int64 if dt == "i32" else torch.float32, device="cuda")
+            cub_fn = cmp.cmp_cub_sum_i32 if dt == "i32" else cmp.cmp_cub_sum_f32
+
+            def cub_call():
+                libcmp.check(cub_fn(x.data_ptr(), n, cub_out.data_ptr(), torch.cuda.current_stream().cuda_stream),
+                             "cub")
+            warm = graph_time(cub_call, calls)
+            both = graph_time(lambda: (flush.fill_(1), cub_call()), max(4, calls // 10))
+            cold = max(both - fl_ms, 1e-6)
+            _emit({"suite": "sweep", "dtype": dt, "log2n": k, "variant": "cub DeviceReduce (library reference)",
+                   "warm_us": round(warm * 1e3, 2), "cold_us": round(cold * 1e3, 2),
+                   "warm_gbs": round(n * 4 / (warm * 1e-3) / 1e9, 1),
+                   "cold_gbs": round(n * 4 / (cold * 1e-3) / 1e9, 1)})
             # library reference point (not on the path): PyTorch's own reduction kernel
             if dt == "f32":
                 try:

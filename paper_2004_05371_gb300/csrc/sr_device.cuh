@@ -247,6 +247,17 @@ __device__ __forceinline__ double to_double(long long v) { return (double)v; }
 __device__ __forceinline__ float to_float(float v) { return v; }
 __device__ __forceinline__ float to_float(Pair v) { return __fadd_rn(v.s, v.c); }
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel launched with the programmatic-stream-serialisation attribute may
+// start while the kernel before it in the stream is still running.
+// grid_dependency_wait() blocks until that kernel has completed and its
+// memory operations are visible (an immediate return for an ordinary launch),
+// so it precedes every global-memory access; allow_dependents() lets the next
+// such launch begin as soon as every CTA of this grid has issued it.  The
+// kernel boundary stays a full barrier; only the launch latency overlaps.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ----------------------------------------------------------- mbarrier/TMA
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

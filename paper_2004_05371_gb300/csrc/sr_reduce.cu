@@ -12,30 +12,50 @@ namespace {
 constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK |
                             SR_F_HOST_DIRECT | SR_F_FP64_AUTO;
 // SR_AUTO's launch shapes, from graph-timed size sweeps and autotuner sweeps
-// on a GB300 (device time per call):
-//   <= 16 KiB : one CTA of 256 threads, 32 B x 2 loads, no grid stage (1.76 us at 16 KiB)
+// on a GB300 (device time per call in a CUDA graph, FP32):
+//   <= 16 KiB : one CTA of 256 threads, 32 B x 2 loads, no grid stage (1.6 us)
 //   <= 1 MiB  : one cluster of 16 such CTAs, DSMEM merge, no grid stage
-//               (1.98 us at 64 KiB, 2.10 at 256 KiB, 2.44 at 1 MiB)
-//   <= 64 MiB : two-kernel form, grid sized by the work      (3.5-15 us)
-//   larger    : last-block-done with the per-dtype shape below (HBM-bound)
+//               (1.8 us at 64 KiB, 2.4 at 1 MiB)
+//   <= 64 MiB : two-kernel form, grid sized by the work, 32 B loads (2.9 us at
+//               4 MiB, 3.5 at 16 MiB, 6.4 at 64 MiB with the input in L2)
+//   larger    : per dtype, below: the two-kernel form with 16 B loads up to
+//               512 MiB, then last-block-done on the TMA ring (HBM-bound)
+// Every launch carries the programmatic-stream-serialisation attribute, so
+// the second kernel of the two-kernel form, and the next call's kernel, are
+// scheduled while their predecessor drains.
 struct AutoShape {
-    int block, vec, unroll;
+    int stage, block, vec, unroll;
     bool bulk;
     int tile, stages;
 };
 constexpr int64_t kAutoOneCtaBytes = 16 << 10;
 constexpr int64_t kAutoClusterBytes = 1 << 20;
 constexpr int64_t kAutoTwoKernelBytes = 64 << 20;
+constexpr int64_t kAutoLdgBytes = 512 << 20;
 
-AutoShape auto_large_shape(int dtype, bool comp) {
+// Above 64 MiB, per dtype, from warm (input streaming from HBM) and cold (L2
+// full of another kernel's dirty lines) sweeps.  Up to 512 MiB the
+// two-kernel form with 16-byte loads and one or two steps in flight per
+// thread; beyond, the TMA ring, as fast as the best LDG shape when streaming
+// and 5-13 % faster when L2 holds dirty lines.  FP8: the LDG shapes win at
+// every size.
+AutoShape auto_large_shape(int dtype, bool comp, int64_t bytes, bool allow_bulk) {
+    const bool ldg = bytes <= kAutoLdgBytes || !allow_bulk;
     if (comp) {
-        if (dtype == SR_F32) return {544, 16, 4, true, 32 << 10, 4};
-        if (dtype == SR_BF16) return {544, 16, 4, true, 64 << 10, 3};
-        return {1024, 16, 2, false, 0, 0};  // FP8: four values per word sum exactly
+        if (dtype == SR_F32)
+            return ldg ? AutoShape{SR_TWO_KERNEL, 1024, 16, 1, false, 0, 0}
+                       : AutoShape{SR_LAST_BLOCK, 544, 16, 4, true, 32 << 10, 4};
+        if (dtype == SR_BF16)
+            return ldg ? AutoShape{SR_TWO_KERNEL, 1024, 16, 1, false, 0, 0}
+                       : AutoShape{SR_LAST_BLOCK, 544, 16, 4, true, 64 << 10, 3};
+        return {SR_LAST_BLOCK, 1024, 16, 2, false, 0, 0};  // FP8: four values per word sum exactly
     }
-    if (dtype == SR_BF16) return {512, 32, 2, false, 0, 0};
-    if (dtype == SR_FP8E4M3) return {1024, 16, 4, false, 0, 0};
-    return {512, 32, 8, false, 0, 0};  // FP32, int32
+    if (dtype == SR_BF16)
+        return ldg ? AutoShape{SR_TWO_KERNEL, 512, 16, 2, false, 0, 0}
+                   : AutoShape{SR_LAST_BLOCK, 544, 16, 1, true, 64 << 10, 2};
+    if (dtype == SR_FP8E4M3) return {SR_LAST_BLOCK, 1024, 16, 4, false, 0, 0};
+    return ldg ? AutoShape{SR_TWO_KERNEL, 512, 16, 1, false, 0, 0}  // FP32, int32
+               : AutoShape{SR_LAST_BLOCK, 160, 16, 1, true, 32 << 10, 4};
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -104,10 +124,18 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
             def_unroll = 2;
         } else if (bytes <= kAutoTwoKernelBytes) {
             p.stage = SR_TWO_KERNEL;
+            if (!p.comp) {
+                // 256-bit loads: inputs of this size are often still in L2,
+                // where wider requests double the throughput
+                def_vec = 32;
+                def_unroll = bytes >= (16 << 20) ? 8 : 2;
+            }
         } else {
             p.stage = SR_LAST_BLOCK;
             if (!p.bulk && !chosen_cluster) {
-                const AutoShape a = auto_large_shape(dtype, p.comp);
+                // explicit vector width or unroll ask for the LDG path
+                const AutoShape a = auto_large_shape(dtype, p.comp, bytes, !c.vec_bytes && !c.unroll);
+                p.stage = a.stage;
                 p.bulk = a.bulk;
                 def_block = a.block;
                 def_vec = a.vec;
@@ -251,36 +279,48 @@ int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, 
         return SR_OK;
     }
 
+    // Both kernels are launched with programmatic stream serialisation: each
+    // may be scheduled while its predecessor in the stream runs, and waits in
+    // grid_dependency_wait() for that predecessor's completion before it
+    // touches global memory.
     cudaLaunchConfig_t lc;
     std::memset(&lc, 0, sizeof lc);
     lc.gridDim = dim3(p.grid);
     lc.blockDim = dim3(p.block);
     lc.dynamicSmemBytes = p.smem;
     lc.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
     if (p.cluster > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = p.cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        lc.attrs = attr;
-        lc.numAttrs = 1;
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = p.cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cudaLaunchConfig_t q = lc;  // the occupancy query sees the cluster shape alone
+        q.attrs = attr + 1;
+        q.numAttrs = 1;
         int nclusters = 0;
-        st = active_clusters(d, ks.main, &lc, &nclusters);
+        st = active_clusters(d, ks.main, &q, &nclusters);
         if (st != SR_OK) return st;
         if (nclusters < 1) return SR_ERR_LAUNCH;
+        lc.numAttrs = 2;
     }
     e = cudaLaunchKernelExC(&lc, ks.main, args);
     if (e != cudaSuccess) return status_from_cuda(e);
 
     if (p.stage == SR_TWO_KERNEL && !skip_final) {
-        // The implicit barrier: stream order makes kernel 2 wait for every
-        // CTA of kernel 1 (Section III-B-2).
+        // The implicit barrier (Section III-B-2): kernel 2 reads the partials
+        // only after kernel 1 has completed — grid_dependency_wait() at its top.
         const int threads = std::min(1024, std::max(32, ((p.units + 31) / 32) * 32));
         std::memset(&lc, 0, sizeof lc);
         lc.gridDim = dim3(1);
         lc.blockDim = dim3(threads);
         lc.stream = s;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
         e = cudaLaunchKernelExC(&lc, ks.final, args);
         if (e != cudaSuccess) return status_from_cuda(e);
     }

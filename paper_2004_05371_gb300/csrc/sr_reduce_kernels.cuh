@@ -205,6 +205,8 @@ template <int DT, bool COMP, int VB, int UNROLL>
 __global__ void __launch_bounds__(1024) reduce_ldg_kernel(const KParams p) {
     using A = typename Acc<DT, COMP>::T;
     constexpr int W = VB / 4;
+    grid_dependency_wait();
+    allow_dependents();
     A acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = Op<A>::zero();
@@ -262,6 +264,8 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
         }
         mbar_fence_init();
     }
+    grid_dependency_wait();  // shared-memory set-up above overlaps the previous kernel
+    allow_dependents();
     __syncthreads();
 
     const int64_t my_tiles = p.ntiles > (int64_t)blockIdx.x
@@ -347,6 +351,8 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
 
 // ---------------------------------------------- two-kernel second stage
 template <class P> __global__ void __launch_bounds__(1024) reduce_final_kernel(const KParams p) {
+    grid_dependency_wait();  // the implicit barrier: every unit's partial is written
+    allow_dependents();
     reduce_slots<P>(p);
 }
 

@@ -13,21 +13,24 @@ pytestmark = pytest.mark.gpu
 
 def test_plan_auto_regimes(sr):
     """SR_AUTO: one CTA up to 16 KiB, a 16-CTA cluster up to 1 MiB, the
-    two-kernel form up to 64 MiB, then last-block-done (FP32 sizes)."""
+    two-kernel form up to 512 MiB, then last-block-done on the TMA ring
+    (FP32 sizes)."""
     cases = [(1 << 10, sr.SINGLE_CLUSTER, 0), (1 << 12, sr.SINGLE_CLUSTER, 0), (1 << 14, sr.SINGLE_CLUSTER, 4),
              (1 << 18, sr.SINGLE_CLUSTER, 4), (1 << 20, sr.TWO_KERNEL, 0), (1 << 24, sr.TWO_KERNEL, 0),
-             (1 << 26, sr.LAST_BLOCK, 0), (1 << 28, sr.LAST_BLOCK, 0)]
+             (1 << 26, sr.TWO_KERNEL, 0), (1 << 27, sr.TWO_KERNEL, 0), (1 << 28, sr.LAST_BLOCK, 0)]
     for n, stage, log2c in cases:
         r = sr.plan(n, sr.F32)
         assert r.variant & sr.STAGE_MASK == stage, n
         assert (r.variant & sr.CLUSTER_MASK) >> sr.CLUSTER_SHIFT == log2c, n
+    r = sr.plan(1 << 27, sr.F32)
+    assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 1, 512) and not r.variant & sr.F_BULK
     r = sr.plan(1 << 28, sr.F32)
-    assert (r.vec_bytes, r.unroll, r.block_threads) == (32, 8, 512)
+    assert r.variant & sr.F_BULK and (r.tile_bytes, r.stages, r.block_threads) == (32768, 4, 160)
     r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.F_KAHAN))
     assert r.variant & sr.F_BULK and r.tile_bytes == 32768 and r.stages == 4
-    # explicit fields override the table
-    r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.AUTO, vec_bytes=16, unroll=2))
-    assert (r.vec_bytes, r.unroll) == (16, 2)
+    # explicit fields override the table; a vector width or unroll selects the LDG path
+    r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.AUTO, vec_bytes=32, unroll=2))
+    assert (r.vec_bytes, r.unroll) == (32, 2) and not r.variant & sr.F_BULK
 
 
 def test_autotune_times_every_candidate(sr):
