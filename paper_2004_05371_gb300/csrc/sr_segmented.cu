@@ -102,18 +102,32 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
         if (e != cudaSuccess) return status_from_cuda(e);
     }
     void* args[] = {&kp};
+    // programmatic stream serialisation, as for the single-array kernels: a
+    // kernel may be scheduled while its predecessor drains and waits for it
+    // in grid_dependency_wait() before touching global memory
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof lc);
+    lc.stream = s;
+    lc.attrs = pdl;
+    lc.numAttrs = 1;
     if (p.stage == SR_GRID_SYNC) {
         e = cudaLaunchCooperativeKernel(p.main, dim3(p.grid), dim3(p.block), args, 0, s);
     } else {
-        e = cudaLaunchKernel(p.main, dim3(p.grid), dim3(p.block), args, 0, s);
+        lc.gridDim = dim3(p.grid);
+        lc.blockDim = dim3(p.block);
+        e = cudaLaunchKernelExC(&lc, p.main, args);
     }
     if (e != cudaSuccess) return status_from_cuda(e);
     if (p.stage == SR_TWO_KERNEL) {
         int64_t wn = p.warps;
         int pv = p.vec / elem_size(p.dtype);
         void* fargs[] = {&kp, &wn, &pv};
-        const int fblocks = (int)((p.warps * 32 + 255) / 256);
-        e = cudaLaunchKernel(p.fin, dim3(fblocks), dim3(256), fargs, 0, s);
+        lc.gridDim = dim3((unsigned)((p.warps * 32 + 255) / 256));
+        lc.blockDim = dim3(256);
+        e = cudaLaunchKernelExC(&lc, p.fin, fargs);
         if (e != cudaSuccess) return status_from_cuda(e);
     }
     return SR_OK;

@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     constexpr int PV = VB / EB;  // elements per lane vector
     constexpr int W = VB / 4;    // 32-bit words per lane vector
     constexpr int RW = 32 * PV;  // elements per row
+    grid_dependency_wait();
+    allow_dependents();
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t Wn = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -349,6 +351,8 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
 template <int DT, bool COMP>
 __global__ void __launch_bounds__(256) seg_finish_kernel(const SegParams p, int64_t Wn, int PV) {
     using A = typename Acc<DT, COMP>::T;
+    grid_dependency_wait();  // the implicit barrier: every first-kernel warp has finished
+    allow_dependents();
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= Wn) return;
