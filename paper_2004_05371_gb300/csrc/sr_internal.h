@@ -86,6 +86,12 @@ int active_clusters(const DeviceInfo& d, const void* fn, const cudaLaunchConfig_
 
 inline int elem_size(int dtype) { return dtype == SR_BF16 ? 2 : (dtype == SR_FP8E4M3 ? 1 : 4); }
 
+// Zeroes `bytes` (a multiple of 4, 4-byte aligned) at device address p with a
+// small kernel launched with programmatic stream serialisation, ordered after
+// the stream's previous work (sr_reduce.cu).  Used where the atomic finish
+// needs a zeroed output: a memset node costs several microseconds more.
+int launch_zero(void* p, size_t bytes, cudaStream_t s);
+
 // Single-array reduction (sr_reduce.cu)
 int reduce_validate(const void* x, int64_t n, int dtype, const void* out, const sr_config& cfg);
 int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& cfg, const DeviceInfo& d, Plan* p);

@@ -2,12 +2,24 @@
 #include <algorithm>
 #include <cstring>
 
+#include "sr_device.cuh"
 #include "sr_internal.h"
 #include "sr_kparams.h"
 
 namespace sr {
 
 namespace {
+
+// The output of an atomic finish starts at zero: this kernel writes it.  It
+// waits for the stream's previous kernel like every kernel of the library,
+// and lets the reduction kernel after it be scheduled at once.
+__global__ void __launch_bounds__(256) zero_words_kernel(uint32_t* p, int64_t nwords) {
+    grid_dependency_wait();
+    allow_dependents();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
 
 constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_BULK |
                             SR_F_HOST_DIRECT | SR_F_FP64_AUTO;
@@ -261,8 +273,8 @@ int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, 
 
     if (p.stage == SR_ATOMIC) {
         const size_t ob = (p.dtype == SR_I32 || p.fp64) ? 8 : 4;
-        e = cudaMemsetAsync(out, 0, ob, s);
-        if (e != cudaSuccess) return status_from_cuda(e);
+        st = launch_zero(out, ob, s);
+        if (st != SR_OK) return st;
     }
 
     void* args[] = {&kp};
@@ -325,6 +337,25 @@ int reduce_launch(const void* x, void* out, const Plan& p, const DeviceInfo& d, 
         if (e != cudaSuccess) return status_from_cuda(e);
     }
     return SR_OK;
+}
+
+int launch_zero(void* p, size_t bytes, cudaStream_t s) {
+    const int64_t nwords = (int64_t)(bytes / 4);
+    if (nwords == 0) return SR_OK;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof lc);
+    lc.gridDim = dim3((unsigned)std::min<int64_t>(cdiv(nwords, 256), 1024));
+    lc.blockDim = dim3(256);
+    lc.stream = s;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    uint32_t* w = static_cast<uint32_t*>(p);
+    void* args[] = {&w, const_cast<int64_t*>(&nwords)};
+    cudaError_t e = cudaLaunchKernelExC(&lc, (const void*)zero_words_kernel, args);
+    return e == cudaSuccess ? SR_OK : status_from_cuda(e);
 }
 
 int reduce_launch_final(const Plan& p, int units, void* out, const Workspace& ws, cudaStream_t s) {

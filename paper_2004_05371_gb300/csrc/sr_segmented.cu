@@ -98,8 +98,8 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
     cudaError_t e;
     if (p.stage == SR_ATOMIC) {
         const size_t ob = (p.dtype == SR_I32 || p.fp64) ? 8 : 4;
-        e = cudaMemsetAsync(out, 0, ob * (size_t)p.nseg, s);
-        if (e != cudaSuccess) return status_from_cuda(e);
+        const int zs = launch_zero(out, ob * (size_t)p.nseg, s);
+        if (zs != SR_OK) return zs;
     }
     void* args[] = {&kp};
     // programmatic stream serialisation, as for the single-array kernels: a

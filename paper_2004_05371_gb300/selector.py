@@ -131,15 +131,17 @@ def train(X, Q, hidden=64, steps=3000, batch=256, lr=3e-3, seed=0, device="cuda"
 
 
 def default_model_params(sms):
-    """Performance-model parameters for a GB300: HBM throughput of the
-    single-array reduction at 2^28 elements, kernel-boundary overhead (Eq. 6)
-    and grid.sync cost measured with sr_barrier_bench; memory latency and the
-    last-block, atomic, per-CTA and per-segment terms are hand-set starting
-    values (see fit_model_params)."""
-    # atomic_ns includes the memset node that zeroes `out` before an atomic finish;
-    # last_block_ns the __threadfence + ticket + final reduction of the last unit
-    return ModelParams(sms=sms, hbm_bytes_per_ns=6900.0, mem_latency_ns=900.0, launch_ns=2250.0,
-                       grid_sync_ns=1150.0, last_block_ns=1500.0, atomic_ns=2500.0, per_cta_ns=4.0,
+    """Performance-model parameters for a GB300.  HBM throughput: the
+    single-array reduction at 2^28 elements.  The finishing costs are measured
+    as the extra device time of each grid stage over a one-CTA call at 2^10
+    elements in a CUDA graph of back-to-back calls (programmatic dependent
+    launch on): a second kernel ~1.0 us (launch_ns, also the base launch),
+    the atomic finish with its output-zeroing kernel ~0.7 us, last-block-done
+    (fence, ticket, final reduction) ~1.5 us, a cooperative launch with
+    grid.sync ~1.8 us.  Memory latency and the per-CTA and per-segment terms
+    are hand-set starting values (see fit_model_params)."""
+    return ModelParams(sms=sms, hbm_bytes_per_ns=6900.0, mem_latency_ns=900.0, launch_ns=1000.0,
+                       grid_sync_ns=1800.0, last_block_ns=1500.0, atomic_ns=700.0, per_cta_ns=4.0,
                        per_segment_ns=150.0)
 
 
