@@ -61,7 +61,8 @@ typedef enum {
     SR_TWO_KERNEL = 1,     /* implicit barrier: kernel 1 writes one partial per unit,
                               kernel 2 (one block) reduces them (Section III-B-2, VII-E) */
     SR_ATOMIC = 2,         /* each unit atomically adds its partial into out (out is
-                              zeroed first); FP order is not deterministic */
+                              zeroed first by a one-line kernel on the same stream);
+                              FP order is not deterministic */
     SR_LAST_BLOCK = 3,     /* partial store, __threadfence, ticket; the last unit to
                               arrive reduces all partials (one kernel, no spin) */
     SR_GRID_SYNC = 4,      /* cooperative persistent kernel: partials, grid.sync(),
