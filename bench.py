@@ -217,7 +217,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=N_HEADLINE, help="elements (profiling runs use a smaller case)")
     ap.add_argument("--skip-extras", action="store_true", help="headline loop only (profiling runs)")
-    ap.add_argument("--suite", default=None, choices=["selector", "barrier", "precision", "sweep", "segmented"],
+    ap.add_argument("--suite", default=None, choices=["selector", "barrier", "precision", "sweep", "segmented", "shapes"],
                     help="secondary measurement suites (JSON lines); the default run is the headline")
     ap.add_argument("--soak-seconds", type=float, default=0.5,
                     help="untimed back-to-back load before the timed region (clock sampling window)")
@@ -337,6 +337,10 @@ def main():
             secondary["latency_2p14_us"] = latency_small(sr, torch, dev, stream)
         except Exception as e:  # reported, never hides the headline
             secondary["latency_2p14_error"] = str(e)[:200]
+        try:
+            secondary["library_reference"] = cub_reference(torch, x, N, stream, args)
+        except Exception as e:
+            secondary["library_reference_error"] = str(e)[:200]
         try:
             secondary["batched_vs_plain"] = batched_vs_plain(sr, torch, dev, stream)
         except Exception as e:
@@ -498,6 +502,33 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
                                "block": r.block_threads, "vec_bytes": r.vec_bytes, "unroll": r.unroll,
                                "chosen_by": "sr_autotune over %d candidates (%.0f us best, %.0f us default)"
                                             % (len(cands), us[best], default_us)}}
+
+
+def cub_reference(torch, x, n, stream, args):
+    """CUB's DeviceReduce::Sum on the same resident input with the headline's
+    protocol (K back-to-back calls between two events after W warm-ups): a
+    library point of comparison, never on the library's path."""
+    import libcmp
+    libcmp.build()
+    cmp = libcmp.lib()
+    libcmp.check(cmp.cmp_prepare(n), "cmp_prepare")
+    out = torch.empty((), dtype=torch.float32, device=x.device)
+    sh = stream.cuda_stream
+
+    def call():
+        libcmp.check(cmp.cmp_cub_sum_f32(x.data_ptr(), n, out.data_ptr(), sh), "cmp_cub_sum_f32")
+    for _ in range(max(3, args.warmup)):
+        call()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        call()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    return {"cub_device_reduce_us": round(ms * 1e3, 2), "gbs": round(n * 4 / (ms * 1e-3) / 1e9, 1),
+            "result": float(out.item())}
 
 
 def end_to_end(sr, torch, dev, stream, x_host, args):

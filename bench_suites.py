@@ -9,6 +9,8 @@
               the exact sum and the FP64 oracle, and throughput
   sweep     : size sweep 2^10..2^30 for FP32 and int32, every grid stage
   segmented : the batched segmented workload in one graph launch per step
+  shapes    : warm / cold launch-shape sweeps per dtype and size (the basis of
+              SR_AUTO's table), SR_AUTO and CUB beside them
 """
 import json
 import math
@@ -174,6 +176,88 @@ def precision_suite(args):
     return 0
 
 
+def _graph_time(torch, stream, body, calls, reps=3):
+    """Device time per call (ms) of `body` captured `calls` times into one
+    CUDA graph on `stream`, averaged over `reps` replays after one warm replay."""
+    with torch.cuda.stream(stream):
+        body()                       # warm-up (allocates the stream's workspace)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(calls):
+            body()
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / (reps * calls)
+
+
+def shapes_suite(args):
+    """The sweeps behind SR_AUTO's table: graph-timed warm (same input every
+    call) and cold (each call after a 256 MiB write, the write's own time
+    subtracted) device time of LDG shapes (two-kernel and last-block; block
+    256/512/1024 x vector 16/32 B x unroll 1/2/4/8, resident CTAs per SM from
+    occupancy) and TMA-ring shapes, per dtype, size and compensation; SR_AUTO
+    and, for FP32 / int32, CUB's DeviceReduce beside them."""
+    import itertools
+    import torch
+    import libcmp
+    import paper_2004_05371_gb300 as sr
+    sr.load()
+    libcmp.build()
+    cmp = libcmp.lib()
+    libcmp.check(cmp.cmp_prepare(1 << 30), "cmp_prepare")
+    big = torch.empty(1 << 30, dtype=torch.float32, device="cuda").uniform_(-1, 1)  # 4 GiB of input bytes
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    fl = _graph_time(torch, s, lambda: flush.fill_(1), 20)
+    out = torch.empty((), dtype=torch.float64, device="cuda")
+    K = sr.F_KAHAN
+    eb = {sr.F32: 4, sr.I32: 4, sr.BF16: 2, sr.FP8E4M3: 1}
+    cases = [(sr.F32, 0, k) for k in (20, 22, 24, 26, 27, 28, 30)] + [(sr.F32, K, k) for k in (26, 27, 28, 30)]
+    cases += [(dt, c, k) for dt in (sr.BF16, sr.FP8E4M3) for c in (0, K) for k in (28, 30)]
+    for dt, comp, k in cases:
+        n = 1 << k
+        calls = 40 if k <= 22 else (8 if k <= 26 else 3)
+        cfgs = [("auto", sr.make_config(sr.AUTO | comp))]
+        for st, blk, vec, un in itertools.product((sr.TWO_KERNEL, sr.LAST_BLOCK), (256, 512, 1024), (16, 32),
+                                                  (1, 2, 4, 8)):
+            cfgs.append(("%s %dx%dB u%d" % ("two_kernel" if st == sr.TWO_KERNEL else "last_block", blk, vec, un),
+                         sr.make_config(st | comp, block_threads=blk, vec_bytes=vec, unroll=un)))
+        for t, stg, blk in ((32768, 4, 160), (32768, 4, 544), (65536, 2, 288), (65536, 2, 544), (65536, 3, 544),
+                            (16384, 6, 288)):
+            cfgs.append(("last_block ring %dKx%d %d" % (t >> 10, stg, blk),
+                         sr.make_config(sr.LAST_BLOCK | sr.F_BULK | comp, tile_bytes=t, stages=stg, block_threads=blk)))
+        res = []
+
+        def timed(name, fn):
+            try:
+                w = _graph_time(torch, s, fn, calls)
+                c = _graph_time(torch, s, lambda: (flush.fill_(1), fn()), calls) - fl
+            except Exception:
+                torch.cuda.synchronize()
+                return
+            res.append((name, round(w * 1e3, 2), round(c * 1e3, 2)))
+        for name, cfg in cfgs:
+            timed(name, lambda cfg=cfg: sr.check(sr.reduce_sum_ptr(big.data_ptr(), n, dt, out.data_ptr(), cfg,
+                                                                   torch.cuda.current_stream().cuda_stream)))
+        if dt == sr.F32 and not comp:
+            timed("cub", lambda: libcmp.check(cmp.cmp_cub_sum_f32(big.data_ptr(), n, out.data_ptr(),
+                                                                   torch.cuda.current_stream().cuda_stream), "cub"))
+        bw = min(r[1] for r in res)
+        bc = min(r[2] for r in res)
+        _emit({"suite": "shapes", "dtype": dt, "compensated": bool(comp), "log2n": k, "bytes": n * eb[dt],
+               "auto": [r for r in res if r[0] == "auto"], "cub": [r for r in res if r[0] == "cub"],
+               "best_warm": sorted(res, key=lambda r: r[1])[:4], "best_cold": sorted(res, key=lambda r: r[2])[:4],
+               "best_both": sorted(res, key=lambda r: max(r[1] / bw, r[2] / bc))[:4]})
+    return 0
+
+
 def sweep_suite(args):
     """Device time per call, from CUDA graphs of back-to-back calls (no host
     launch cost): warm = the same input every call; cold = each call preceded
@@ -192,22 +276,7 @@ def sweep_suite(args):
     s = torch.cuda.Stream()
 
     def graph_time(body, calls):
-        with torch.cuda.stream(s):
-            body()                       # warm-up (allocates the stream's workspace)
-        s.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            for _ in range(calls):
-                body()
-        g.replay()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(3):
-            g.replay()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / (3 * calls)   # ms per call
+        return _graph_time(torch, s, body, calls)
 
     fl_ms = graph_time(lambda: flush.fill_(1), 20)
     for dt, src in (("f32", big), ("i32", bigi)):
@@ -302,5 +371,5 @@ def segmented_suite(args):
 
 
 def run(name, args):
-    return {"selector": selector_suite, "barrier": barrier_suite, "precision": precision_suite,
+    return {"selector": selector_suite, "barrier": barrier_suite, "precision": precision_suite, "shapes": shapes_suite,
             "sweep": sweep_suite, "segmented": segmented_suite}[name](args)

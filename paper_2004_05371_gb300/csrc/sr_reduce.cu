@@ -49,8 +49,8 @@ constexpr int64_t kAutoLdgBytes = 512 << 20;
 // full of another kernel's dirty lines) sweeps.  Up to 512 MiB the
 // two-kernel form with 16-byte loads and one or two steps in flight per
 // thread; beyond, the TMA ring, as fast as the best LDG shape when streaming
-// and 5-13 % faster when L2 holds dirty lines.  FP8: the LDG shapes win at
-// every size.
+// and 5-13 % faster when L2 holds dirty lines.  FP8: LDG shapes at every
+// size (the decode, not the copy, sets the pace).
 AutoShape auto_large_shape(int dtype, bool comp, int64_t bytes, bool allow_bulk) {
     const bool ldg = bytes <= kAutoLdgBytes || !allow_bulk;
     if (comp) {
@@ -65,7 +65,9 @@ AutoShape auto_large_shape(int dtype, bool comp, int64_t bytes, bool allow_bulk)
     if (dtype == SR_BF16)
         return ldg ? AutoShape{SR_TWO_KERNEL, 512, 16, 2, false, 0, 0}
                    : AutoShape{SR_LAST_BLOCK, 544, 16, 1, true, 64 << 10, 2};
-    if (dtype == SR_FP8E4M3) return {SR_LAST_BLOCK, 1024, 16, 4, false, 0, 0};
+    if (dtype == SR_FP8E4M3)
+        return ldg ? AutoShape{SR_TWO_KERNEL, 512, 16, 1, false, 0, 0}
+                   : AutoShape{SR_TWO_KERNEL, 1024, 16, 1, false, 0, 0};
     return ldg ? AutoShape{SR_TWO_KERNEL, 512, 16, 1, false, 0, 0}  // FP32, int32
                : AutoShape{SR_LAST_BLOCK, 160, 16, 1, true, 32 << 10, 4};
 }
