@@ -11,6 +11,8 @@
   segmented : the batched segmented workload in one graph launch per step
   shapes    : warm / cold launch-shape sweeps per dtype and size (the basis of
               SR_AUTO's table), SR_AUTO and CUB beside them
+  seglayouts: the segmented kernel over sparse to dense segment layouts, with and
+              without SR_F_DENSE_SEGMENTS
 """
 import json
 import math
@@ -370,6 +372,49 @@ def segmented_suite(args):
     return 0
 
 
+def seglayouts_suite(args):
+    """The segmented kernel across layouts at ~2^28 FP32 elements: 10,000 and
+    100,000 lognormal segments, 1M / 4M / 16M equal ones (268, 64 and 16
+    elements), 4M lognormal short ones (median 40, empty ones included); the
+    default kernel and SR_F_DENSE_SEGMENTS, two launch shapes, atomic finish;
+    device time per call in a CUDA graph."""
+    import torch
+    import paper_2004_05371_gb300 as sr
+    import workloads
+    sr.load()
+    N = 1 << 28
+    NX = N + (1 << 22)  # lognormal totals land within 1 % of N: the buffer covers offsets[nseg]
+    x = torch.empty(NX, dtype=torch.float32, device="cuda").uniform_(-1, 1)
+    s = torch.cuda.Stream()
+    cases = [("10k lognormal (median 4096)", workloads.segment_offsets(10_000, N, seed=0)),
+             ("100k lognormal (median 2684)", workloads.segment_offsets(100_000, N, seed=0, median=N // 100_000)),
+             ("1M equal (268)", np.linspace(0, N, 1_000_001).astype(np.int64)),
+             ("4M equal (64)", np.arange(4_194_305, dtype=np.int64) * 64),
+             ("16M equal (16)", np.arange(16_777_217, dtype=np.int64) * 16),
+             ("4M lognormal (median 40, empties)",
+              workloads.segment_offsets(4 << 20, N, seed=3, median=40, sigma=1.5, lo=0, hi=1 << 16))]
+    for name, off in cases:
+        nseg, n = len(off) - 1, int(off[-1])
+        if n > NX:
+            raise RuntimeError("layout %s needs %d elements, buffer holds %d" % (name, n, NX))
+        od = torch.from_numpy(off).cuda()
+        out = torch.empty(nseg, dtype=torch.float32, device="cuda")
+        for shape in ((256, 32, 8), (512, 32, 4)):
+            for dense in (0, sr.F_DENSE_SEGMENTS):
+                cfg = sr.make_config(sr.ATOMIC | dense, block_threads=shape[0], vec_bytes=shape[1], unroll=shape[2])
+
+                def call(cfg=cfg):
+                    sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(),
+                                                         cfg, torch.cuda.current_stream().cuda_stream))
+                ms = _graph_time(torch, s, call, 5, reps=4)
+                _emit({"suite": "seglayouts", "layout": name, "nseg": nseg, "n": n, "dense": bool(dense),
+                       "shape": "%d threads x %d B x unroll %d" % shape, "us": round(ms * 1e3, 2),
+                       "gbs": round(n * 4 / (ms * 1e-3) / 1e9, 1)})
+        del od, out
+        torch.cuda.empty_cache()
+    return 0
+
+
 def run(name, args):
     return {"selector": selector_suite, "barrier": barrier_suite, "precision": precision_suite, "shapes": shapes_suite,
-            "sweep": sweep_suite, "segmented": segmented_suite}[name](args)
+            "sweep": sweep_suite, "segmented": segmented_suite, "seglayouts": seglayouts_suite}[name](args)

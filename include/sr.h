@@ -92,6 +92,12 @@ typedef enum {
                                    stays binary32.  Ignored under SR_F_FP64_COMBINE.
                                    Single-array stages with a cross-unit combine
                                    (two-kernel, last-block, grid-sync); not segmented. */
+#define SR_F_DENSE_SEGMENTS 0x2000 /* segmented only: rows of vectors in which three or
+                                   more segments end are resolved in one warp-wide
+                                   segmented scan instead of one warp reduction per
+                                   segment (4x faster at ~16-element segments, 1.4x at
+                                   ~64); for layouts of mostly short segments, slower on
+                                   mixes of tiny and long ones.  Same results contract. */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses

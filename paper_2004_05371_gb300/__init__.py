@@ -25,6 +25,7 @@ F_FP64_COMBINE = 0x200
 F_BULK = 0x400
 F_HOST_DIRECT = 0x800
 F_FP64_AUTO = 0x1000
+F_DENSE_SEGMENTS = 0x2000
 # status codes (sr_status)
 OK, ERR_ARG, ERR_DTYPE, ERR_LAUNCH, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 # barrier levels (sr_level)

@@ -71,16 +71,22 @@ template <> struct Op<long long> {
     __device__ static long long zero() { return 0; }
     __device__ static long long add(long long a, long long b) { return a + b; }
     __device__ static long long shfl_down(long long v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+    __device__ static long long shfl(long long v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    __device__ static long long shfl_up(long long v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 };
 template <> struct Op<float> {
     __device__ static float zero() { return 0.f; }
     __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
     __device__ static float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+    __device__ static float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    __device__ static float shfl_up(float v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 };
 template <> struct Op<double> {
     __device__ static double zero() { return 0.0; }
     __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
     __device__ static double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+    __device__ static double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    __device__ static double shfl_up(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 };
 template <> struct Op<Pair> {
     __device__ static Pair zero() { return Pair{0.f, 0.f}; }
@@ -92,6 +98,12 @@ template <> struct Op<Pair> {
     }
     __device__ static Pair shfl_down(Pair v, int o) {
         return Pair{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+    }
+    __device__ static Pair shfl(Pair v, int src) {
+        return Pair{__shfl_sync(0xffffffffu, v.s, src), __shfl_sync(0xffffffffu, v.c, src)};
+    }
+    __device__ static Pair shfl_up(Pair v, int o) {
+        return Pair{__shfl_up_sync(0xffffffffu, v.s, o), __shfl_up_sync(0xffffffffu, v.c, o)};
     }
 };
 

@@ -63,7 +63,7 @@ struct SegPlan {
     int dtype = 0;
     int64_t nseg = 0;
     int stage = 0;
-    bool comp = false, fp64 = false;
+    bool comp = false, fp64 = false, dense = false;
     int vec = 16, unroll = 4, block = 256, grid = 0;
     int64_t warps = 0;
     float scale = 1.f;

@@ -49,10 +49,10 @@ struct SegParams {
 };
 
 // Per-dtype segmented kernel selection.
-bool seg_kernels_f32(bool comp, int vec, int unroll, const void** main, const void** fin);
-bool seg_kernels_i32(bool comp, int vec, int unroll, const void** main, const void** fin);
-bool seg_kernels_bf16(bool comp, int vec, int unroll, const void** main, const void** fin);
-bool seg_kernels_fp8(bool comp, int vec, int unroll, const void** main, const void** fin);
+bool seg_kernels_f32(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
+bool seg_kernels_i32(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
+bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
+bool seg_kernels_fp8(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
 
 struct KernelSet {
     const void* main = nullptr;   // thread..grid stages

@@ -8,14 +8,14 @@
 namespace sr {
 
 namespace {
-constexpr int kKnownSegFlags = SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE;
+constexpr int kKnownSegFlags = SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_DENSE_SEGMENTS;
 
-bool seg_kernels(int dtype, bool comp, int vec, int unroll, const void** main, const void** fin) {
+bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, const void** main, const void** fin) {
     switch (dtype) {
-    case SR_F32: return seg_kernels_f32(comp, vec, unroll, main, fin);
-    case SR_I32: return seg_kernels_i32(comp, vec, unroll, main, fin);
-    case SR_BF16: return seg_kernels_bf16(comp, vec, unroll, main, fin);
-    case SR_FP8E4M3: return seg_kernels_fp8(comp, vec, unroll, main, fin);
+    case SR_F32: return seg_kernels_f32(comp, vec, unroll, dense, main, fin);
+    case SR_I32: return seg_kernels_i32(comp, vec, unroll, dense, main, fin);
+    case SR_BF16: return seg_kernels_bf16(comp, vec, unroll, dense, main, fin);
+    case SR_FP8E4M3: return seg_kernels_fp8(comp, vec, unroll, dense, main, fin);
     default: return false;
     }
 }
@@ -61,7 +61,8 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     p.unroll = c.unroll ? c.unroll : 8;
     p.block = c.block_threads ? c.block_threads : 256;
     p.scale = (dtype == SR_FP8E4M3 && c.scale != 0.f) ? c.scale : 1.f;
-    if (!seg_kernels(dtype, p.comp, p.vec, p.unroll, &p.main, &p.fin)) return SR_ERR_UNSUPPORTED;
+    p.dense = (c.variant & SR_F_DENSE_SEGMENTS) != 0;
+    if (!seg_kernels(dtype, p.comp, p.vec, p.unroll, p.dense, &p.main, &p.fin)) return SR_ERR_UNSUPPORTED;
     int resident = 0;
     int st = blocks_per_sm(d, p.main, p.block, 0, &resident);
     if (st != SR_OK) return st;

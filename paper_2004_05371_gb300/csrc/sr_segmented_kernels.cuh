@@ -178,7 +178,9 @@ template <class A> __device__ __forceinline__ void span_arrive(const SegParams& 
 // is accumulated whole, a row that does takes a masked per-element path and
 // emits each segment that ends in it — the load pipeline never drains at a
 // boundary.
-template <int DT, bool COMP, int VB, int UNROLL>
+constexpr int kScanMin = 3;  // boundaries in a row from which the warp-wide pass pays
+
+template <int DT, bool COMP, int VB, int UNROLL, bool DENSE>
 __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     using A = typename Acc<DT, COMP>::T;
     constexpr int EB = SegElem<DT>::v;
@@ -270,6 +272,91 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
         cur_end = __shfl_sync(0xffffffffu, win, (int)(cur + 1 - wb));
     };
 
+    // A row [c0, c1) in which segments end, every boundary resolved in one
+    // warp-wide pass: each lane splits its vector at the boundary it holds
+    // (head before, tail from it on), a segmented inclusive scan over the lanes
+    // (flag = the lane holds a boundary) yields the run open at the end of
+    // every lane, and the lane holding boundary j emits the segment that ends
+    // there: cur itself for j = 0 (with the rows before folded in), an owned
+    // segment complete inside the row for j >= 1.  The run open at the row's
+    // end becomes the next segment's carry.  Applies when the row holds at
+    // least kScanMin boundaries (below that one warp reduction per boundary is
+    // cheaper than the pass's fixed ~17 shuffle rounds), no lane holds two,
+    // and the offsets window already holds all of them; returns false, having
+    // changed nothing, otherwise (no load is spent on a row that may fail).
+    auto row_scan = [&](int64_t c0, int64_t c1, int64_t e0, bool valid, const uint32_t (&r_words)[W]) -> bool {
+        const int kb = (int)(cur + 1 - wb);  // window lane of the row's first boundary
+        const bool is_b = lane >= kb && win < c1;  // the row's boundaries: lanes kb .. kb + m - 1
+        const unsigned bm = __ballot_sync(0xffffffffu, is_b);
+        if (bm & 0x80000000u) return false;  // more boundaries may follow beyond the window
+        const int m = __popc(bm);
+        if (m < kScanMin) return false;
+        const int tl = is_b ? (int)((win - c0) / PV) : -1;  // lane of the row holding boundary
+        const int tl_next = __shfl_down_sync(0xffffffffu, tl, 1);
+        if (__any_sync(0xffffffffu, is_b && lane < 31 && tl_next == tl)) return false;  // two in one lane
+        const unsigned tmask = __reduce_or_sync(0xffffffffu, is_b ? (1u << tl) : 0u);
+        const bool has_b = (tmask >> lane) & 1u;
+        const int bj = __popc(tmask & ((1u << lane) - 1u));  // this lane's boundary among the row's
+        const int64_t bpos = __shfl_sync(0xffffffffu, win, (kb + bj) & 31);
+        const int q = has_b ? (int)(bpos - e0) : PV;  // elements j < q precede the boundary
+        A head = Op<A>::zero(), tail = Op<A>::zero();
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < PV; ++j) {
+                if (e0 + j < c1) {
+                    if (j < q) acc_vec_elem<DT>(head, r_words, j);
+                    else acc_vec_elem<DT>(tail, r_words, j);
+                }
+            }
+        }
+        // segmented inclusive scan of the open runs over the lanes; before the
+        // step with distance d a lane's partial covers lanes [lane - d + 1,
+        // lane], which holds a boundary exactly when tmask has a bit there
+        A x = has_b ? tail : head;
+        const unsigned upto = (2u << lane) - 1u;  // lanes 0 .. lane (wraps to all ones at 31)
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const A xo = Op<A>::shfl_up(x, d);
+            const int first = lane - d + 1 > 0 ? lane - d + 1 : 0;
+            const bool f = (tmask & upto & ~((1u << first) - 1u)) != 0u;
+            if (lane >= d && !f) x = Op<A>::add(xo, x);
+        }
+        A prev = Op<A>::shfl_up(x, 1);  // the run open at the end of the previous lane
+        if (lane == 0) prev = Op<A>::zero();
+        const A closed = Op<A>::add(prev, head);  // the segment ending at this lane's boundary
+        const A open_end = Op<A>::shfl(x, 31);   // the run open at the row's end
+        const int64_t last_pos = __shfl_sync(0xffffffffu, win, (kb + m - 1) & 31);
+        const int64_t cur0 = cur;
+        // owned segments complete inside the row (boundaries j >= 1)
+        if (has_b && bj >= 1) seg_out(p, cur0 + bj, closed);
+        // segment cur: the rows before this one (acc, per lane) plus its part
+        // of this row, folded into lane 0 and emitted the usual way
+        const A first = Op<A>::shfl(closed, __ffs(tmask) - 1);
+        if (lane == 0) acc[0] = Op<A>::add(acc[0], first);
+        emit_advance();  // cur0 -> cur0 + 1
+        // step over the segments emitted above to the one open at the row's end
+        cur = cur0 + m;
+        cur_start = last_pos;
+        if (cur >= p.nseg) {
+            cur_end = INT64_MAX;
+        } else {
+            const int64_t kc = cur + 1 - wb;
+            if (kc < 32) {
+                cur_end = __shfl_sync(0xffffffffu, win, (int)kc);
+                if (kc >= 16) {  // refill the window ahead: the load overlaps the next rows
+                    wb = cur + 1;
+                    win = (wb + lane <= p.nseg) ? __ldg(p.offsets + wb + lane) : INT64_MAX;
+                }
+            } else {
+                wb = cur + 1;
+                win = (wb + lane <= p.nseg) ? __ldg(p.offsets + wb + lane) : INT64_MAX;
+                cur_end = __shfl_sync(0xffffffffu, win, 0);
+            }
+        }
+        if (lane == 0) acc[0] = open_end;
+        return true;
+    };
+
     // scalar chunk [c0, c1), at most 32 elements: lane l holds element c0 + l
     auto scalar_chunk = [&](int64_t c0, int64_t c1) {
         if (c0 >= c1) return;
@@ -298,7 +385,10 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
             }
             return;
         }
-        for (;;) {  // segments end inside this row
+        if constexpr (DENSE) {
+            if (row_scan(c0, c1, e0, valid, r_words)) return;
+        }
+        for (;;) {  // segments end inside this row (one reduction per segment)
             if (valid) {
                 // element j of the lane's vector belongs to the current segment
                 // when cur_start <= e0 + j < cur_end (static indices keep the
@@ -367,20 +457,26 @@ __global__ void __launch_bounds__(256) seg_finish_kernel(const SegParams p, int6
     finish_span<A>(p, s, w, (end - 1 - base) / E, lane);
 }
 
-template <int DT, bool COMP, int VB>
+template <int DT, bool COMP, int VB, bool DENSE>
 inline const void* pick_seg(int unroll) {
     switch (unroll) {
-    case 1: return (const void*)seg_kernel<DT, COMP, VB, 1>;
-    case 2: return (const void*)seg_kernel<DT, COMP, VB, 2>;
-    case 4: return (const void*)seg_kernel<DT, COMP, VB, 4>;
-    case 8: return (const void*)seg_kernel<DT, COMP, VB, 8>;
+    case 1: return (const void*)seg_kernel<DT, COMP, VB, 1, DENSE>;
+    case 2: return (const void*)seg_kernel<DT, COMP, VB, 2, DENSE>;
+    case 4: return (const void*)seg_kernel<DT, COMP, VB, 4, DENSE>;
+    case 8: return (const void*)seg_kernel<DT, COMP, VB, 8, DENSE>;
     default: return nullptr;
     }
 }
 
+template <int DT, bool COMP, bool DENSE>
+inline const void* pick_seg_vec(int vec, int unroll) {
+    return vec == 16 ? pick_seg<DT, COMP, 16, DENSE>(unroll)
+                     : (vec == 32 ? pick_seg<DT, COMP, 32, DENSE>(unroll) : nullptr);
+}
+
 template <int DT, bool COMP>
-inline bool pick_seg_kernels(int vec, int unroll, const void** main, const void** fin) {
-    *main = vec == 16 ? pick_seg<DT, COMP, 16>(unroll) : (vec == 32 ? pick_seg<DT, COMP, 32>(unroll) : nullptr);
+inline bool pick_seg_kernels(int vec, int unroll, bool dense, const void** main, const void** fin) {
+    *main = dense ? pick_seg_vec<DT, COMP, true>(vec, unroll) : pick_seg_vec<DT, COMP, false>(vec, unroll);
     *fin = (const void*)seg_finish_kernel<DT, COMP>;
     return *main != nullptr;
 }

@@ -14,6 +14,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 STAGES = [1, 2, 3, 4]  # two-kernel, atomic, last-block, grid-sync
+DENSE = 0x2000  # SR_F_DENSE_SEGMENTS: the warp-wide segmented scan over rows with many boundaries
 EPS32 = 2.0 ** -23
 U = 2.0 ** -24
 
@@ -59,8 +60,9 @@ def test_random_layouts(sr, stage, nseg, max_len):
     xi = workloads.uniform_i32(n, seed=1)
     for grid in (0, 1, 3):
         for x_off in (0, 1):
-            _check(sr, xi, off, stage, x_off, grid=grid)
-            _check(sr, xf, off, stage, x_off, grid=grid)
+            for dense in (0, DENSE):
+                _check(sr, xi, off, stage | dense, x_off, grid=grid)
+                _check(sr, xf, off, stage | dense, x_off, grid=grid)
 
 
 @pytest.mark.parametrize("stage", STAGES)
@@ -196,3 +198,52 @@ def test_search_with_exactly_32_candidates_left(sr, nseg):
     x2 = workloads.uniform_i32(int(off2[-1]) + 1, seed=1)
     for st in STAGES:
         _check(sr, x2, off2, st)
+
+
+@pytest.mark.parametrize("stage", STAGES)
+@pytest.mark.parametrize("seg_len", [3, 5, 8, 9, 16, 31, 100, 255, 257])
+def test_rows_with_many_boundaries(sr, stage, seg_len):
+    """Rows in which many segments end: at most one boundary per lane takes
+    the warp-wide segmented scan, two or more in a lane the per-segment path
+    (lengths below the lane vector); both launch-shape families, aligned and
+    misaligned data; bit-exact for int32, within the gates for binary32."""
+    nseg = (1 << 18) // seg_len
+    off = np.arange(nseg + 1, dtype=np.int64) * seg_len
+    n = int(off[-1])
+    xi = workloads.uniform_i32(n, seed=seg_len)
+    xf = workloads.uniform_f32(n, seed=seg_len)
+    for dense in (0, DENSE):
+        for vec, unroll, block in ((32, 8, 256), (16, 2, 128)):
+            for x_off in (0, 1):
+                _check(sr, xi, off, stage | dense, x_off, vec_bytes=vec, unroll=unroll, block_threads=block)
+                _check(sr, xf, off, stage | dense, x_off, vec_bytes=vec, unroll=unroll, block_threads=block)
+        _check(sr, xf, off, stage | 0x100 | dense)
+        _check(sr, xf, off, stage | 0x300 | dense)
+
+
+@pytest.mark.parametrize("stage", STAGES)
+def test_many_small_lognormal_segments(sr, stage):
+    """100,000 lognormal segments (median 40 elements, empty ones included)
+    over ~2^22 elements: rows mixing both boundary paths, every dtype."""
+    off = workloads.segment_offsets(100_000, 1 << 22, seed=12, median=40, sigma=1.5, lo=0, hi=1 << 16)
+    n = int(off[-1])
+    x = workloads.lognormal_f32(n, seed=12, sigma=2.0)
+    bits = workloads.to_bf16_bits(x)
+    dec_b = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+    codes, deq = workloads.to_e4m3_codes(x)
+    od = torch.from_numpy(off).cuda()
+    xd_b = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    xd_f = torch.from_numpy(codes).cuda()
+    ex_b = oracle.segexact_f32(dec_b, off)
+    gate_b = 4 * EPS32 * oracle.segsum_abs_f32(dec_b, off) + 1e-30
+    for dense in (0, DENSE):
+        _check(sr, workloads.uniform_i32(n, seed=12), off, stage | dense)
+        _check(sr, workloads.uniform_f32(n, seed=12), off, stage | dense)
+        got = sr.reduce_sum_segmented(xd_b, od, variant=stage | dense).cpu().numpy()
+        assert np.all(np.abs(got - ex_b) <= gate_b), dense
+        got = sr.reduce_sum_segmented(xd_f, od, config=sr.make_config(stage | dense, scale=deq)).cpu().numpy()
+        for s in range(0, 100_000, 997):
+            a, b = off[s], off[s + 1]
+            exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
+            sabs = oracle.sum_e4m3(codes[a:b] & 0x7F, deq)
+            assert abs(got[s] - exs) <= 4 * EPS32 * sabs * 1.001 + 1e-30, (dense, s)
