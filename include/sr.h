@@ -424,7 +424,9 @@ int sr_selector_choose(sr_selector selector, int64_t n, int dtype, int64_t nseg,
  * candidates on the call's own data the first time its shape is seen
  * (memoised; that first call synchronises `stream`).  Other arguments and
  * errors as sr_reduce_sum_ex / sr_reduce_sum_segmented_ex; the segmented form
- * takes the segment-length statistics from the caller (n = mean * nseg). */
+ * takes the segment-length statistics from the caller (n = mean * nseg) and
+ * adds SR_F_DENSE_SEGMENTS to the chosen configuration when segments are
+ * uniformly short (mean * element size <= 512 bytes and std <= mean / 2). */
 int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int dtype, void* out,
                            sr_stream_t stream);
 int sr_reduce_sum_segmented_selected(sr_selector selector, const void* x, const int64_t* offsets, int64_t nseg,

@@ -153,4 +153,13 @@ def test_selected_entry_points(sr):
         sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), 500, sr.I32, out.data_ptr(),
                                                       lens.mean(), lens.std(), lens.max()))
         assert np.array_equal(out.cpu().numpy(), oracle.segsum_i32(x, off))
+    # uniformly short segments: the selected call adds SR_F_DENSE_SEGMENTS
+    off = np.arange(20_001, dtype=np.int64) * 24
+    x = workloads.uniform_i32(int(off[-1]), seed=5)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
+    out = torch.zeros(20_000, dtype=torch.int64, device="cuda")
+    for s in (nat, None):
+        sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), 20_000, sr.I32, out.data_ptr(),
+                                                      24.0, 0.0, 24.0))
+        assert np.array_equal(out.cpu().numpy(), oracle.segsum_i32(x, off))
     nat.close()
