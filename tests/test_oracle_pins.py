@@ -305,3 +305,22 @@ def test_mlp_oracle_adam_first_step_is_sign_step():
     p1, m, v = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
     # bias-corrected first step: mhat = g, vhat = g^2, so the step is lr * sign(g)
     assert np.allclose(p1, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_mlp_oracle_predict_and_forward_by_hand():
+    """The 1-1-2 network worked by hand: x = 1 gives z = (abc + 0.1, abd + 0.2),
+    class 0 for c > d; x = -1 is cut by the first ReLU, so z = b3 and the
+    class is argmax(b3) = 1."""
+    from oracle import mlp
+    a, b, c, d = 0.7, 1.3, 0.4, -0.9
+    p = np.array([a, 0.0, b, 0.0, c, d, 0.1, 0.2])
+    _, _, z = mlp.forward(p, [[1.0], [-1.0]], (1, 1, 2))
+    assert z[0] == pytest.approx([a * b * c + 0.1, a * b * d + 0.2])
+    assert z[1] == pytest.approx([0.1, 0.2])
+    assert list(mlp.predict(p, [[1.0], [-1.0]], (1, 1, 2))) == [0, 1]
+
+
+def test_segsum_abs_closed_form():
+    x = np.array([1, -2, 3, -4, 5, -6], np.float32)
+    off = np.array([0, 2, 2, 6], np.int64)
+    assert list(oracle.segsum_abs_f32(x, off)) == [3.0, 0.0, 18.0]
