@@ -237,3 +237,44 @@ def test_max_size_2p30_int32_worst_case(sr):
         assert int(sr.reduce_sum(d, variant=st).item()) == n * (2 ** 31 - 1)
     del d
     torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_auto_regime_boundaries(sr):
+    """SR_AUTO on both sides of each of its size thresholds (16 KiB one CTA,
+    1 MiB one cluster, 64 MiB two-kernel with 32-byte loads, 512 MiB two-kernel
+    with 16-byte loads, above: TMA ring or per-dtype LDG) for every dtype,
+    aligned and misaligned: int32 bit-exact, floating point within the gates."""
+    for bound in (16 << 10, 1 << 20, 64 << 20, 512 << 20):
+        big = bound == 512 << 20
+        for dt, es in ((sr.F32, 4), (sr.I32, 4), (sr.BF16, 2), (sr.FP8E4M3, 1)):
+            for d, off in (((1, 1),) if big else ((0, 0), (1, 1), (-1, 3))):
+                n = bound // es + d
+                seed = n % 1000
+                if dt == sr.I32:
+                    x = workloads.uniform_i32(n, seed=seed)
+                    got = int(sr.reduce_sum(_to_dev(x, off)).item())
+                    assert got == oracle.sum_i32(x), (bound, d, off)
+                elif dt == sr.F32:
+                    x = workloads.uniform_f32(n, seed=seed)
+                    got = float(sr.reduce_sum(_to_dev(x, off)).item())
+                    _check_f32(sr, x, got, sr.AUTO)
+                elif dt == sr.BF16:
+                    bits = workloads.to_bf16_bits(workloads.uniform_f32(n, seed=seed))
+                    buf = np.zeros(n + off, np.uint16)
+                    buf[off:] = bits
+                    xd = torch.from_numpy(buf.view(np.int16)).cuda().view(torch.bfloat16)[off:]
+                    got = float(sr.reduce_sum(xd).item())
+                    dec = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+                    ex = oracle.to_float(oracle.exact_bf16(bits))
+                    assert abs(got - ex) <= oracle.stated_fp32_bound(oracle.sum_abs_f32(dec)), (bound, d, off)
+                else:
+                    codes, deq = workloads.to_e4m3_codes(workloads.uniform_f32(n, seed=seed))
+                    buf = np.zeros(n + off, np.uint8)
+                    buf[off:] = codes
+                    xd = torch.from_numpy(buf).cuda()[off:]
+                    got = float(sr.reduce_sum(xd, scale=deq).item())
+                    ex = oracle.to_float(oracle.exact_e4m3(codes, deq))
+                    assert abs(got - ex) <= oracle.stated_fp32_bound(oracle.sum_e4m3(codes & 0x7F, deq)), (bound, d)
+                torch.cuda.empty_cache()
+    assert sr.stream_status() == sr.OK
