@@ -407,8 +407,11 @@ def seglayouts_suite(args):
                     sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(),
                                                          cfg, torch.cuda.current_stream().cuda_stream))
                 ms = _graph_time(torch, s, call, 5, reps=4)
+                r = sr.plan_segmented(nseg, sr.F32, cfg)  # the shape that ran (dense lowers unroll 8 to 4)
                 _emit({"suite": "seglayouts", "layout": name, "nseg": nseg, "n": n, "dense": bool(dense),
-                       "shape": "%d threads x %d B x unroll %d" % shape, "us": round(ms * 1e3, 2),
+                       "shape": "%d threads x %d B x unroll %d" % shape,
+                       "ran": "%d threads x %d B x unroll %d" % (r.block_threads, r.vec_bytes, r.unroll),
+                       "us": round(ms * 1e3, 2),
                        "gbs": round(n * 4 / (ms * 1e-3) / 1e9, 1)})
         del od, out
         torch.cuda.empty_cache()

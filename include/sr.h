@@ -95,9 +95,11 @@ typedef enum {
 #define SR_F_DENSE_SEGMENTS 0x2000 /* segmented only: rows of vectors in which three or
                                    more segments end are resolved in one warp-wide
                                    segmented scan instead of one warp reduction per
-                                   segment (4x faster at ~16-element segments, 1.4x at
-                                   ~64); for layouts of mostly short segments, slower on
-                                   mixes of tiny and long ones.  Same results contract. */
+                                   segment (4.6-6.6x faster at 16-element segments,
+                                   1.6-1.9x at 64); up to 17 % slower where few rows
+                                   qualify.  512-thread CTAs by default; runs at most 4 rows in
+                                   flight per warp (unroll 8 is lowered to 4; sr_plan_
+                                   segmented reports it).  Same results contract. */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses

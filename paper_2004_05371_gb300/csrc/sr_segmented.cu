@@ -62,6 +62,10 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     p.block = c.block_threads ? c.block_threads : 256;
     p.scale = (dtype == SR_FP8E4M3 && c.scale != 0.f) ? c.scale : 1.f;
     p.dense = (c.variant & SR_F_DENSE_SEGMENTS) != 0;
+    if (p.dense) {  // the dense kernel runs at most 4 rows in flight; 512-thread CTAs by default
+        if (p.unroll > 4) p.unroll = 4;
+        if (!c.block_threads) p.block = 512;
+    }
     if (!seg_kernels(dtype, p.comp, p.vec, p.unroll, p.dense, &p.main, &p.fin)) return SR_ERR_UNSUPPORTED;
     int resident = 0;
     int st = blocks_per_sm(d, p.main, p.block, 0, &resident);

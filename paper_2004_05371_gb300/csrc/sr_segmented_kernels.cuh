@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     // (head before, tail from it on), a segmented inclusive scan over the lanes
     // (flag = the lane holds a boundary) yields the run open at the end of
     // every lane, and the lane holding boundary j emits the segment that ends
-    // there: cur itself for j = 0 (with the rows before folded in), an owned
+    // there: cur itself for j = 0 (with the rows before folded in; cur must be
+    // owned by this warp, a continuation takes the per-segment path), an owned
     // segment complete inside the row for j >= 1.  The run open at the row's
     // end becomes the next segment's carry.  Applies when the row holds at
     // least kScanMin boundaries (below that one warp reduction per boundary is
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     // and the offsets window already holds all of them; returns false, having
     // changed nothing, otherwise (no load is spent on a row that may fail).
     auto row_scan = [&](int64_t c0, int64_t c1, int64_t e0, bool valid, const uint32_t (&r_words)[W]) -> bool {
+        if (cur_start < lo) return false;  // cur continues an earlier warp's segment: per-segment path
         const int kb = (int)(cur + 1 - wb);  // window lane of the row's first boundary
         const bool is_b = lane >= kb && win < c1;  // the row's boundaries: lanes kb .. kb + m - 1
         const unsigned bm = __ballot_sync(0xffffffffu, is_b);
@@ -329,11 +331,16 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
         const int64_t cur0 = cur;
         // owned segments complete inside the row (boundaries j >= 1)
         if (has_b && bj >= 1) seg_out(p, cur0 + bj, closed);
-        // segment cur: the rows before this one (acc, per lane) plus its part
-        // of this row, folded into lane 0 and emitted the usual way
+        // segment cur, owned by this warp and complete: the rows before this
+        // one (acc, per lane) plus its part of this row
         const A first = Op<A>::shfl(closed, __ffs(tmask) - 1);
-        if (lane == 0) acc[0] = Op<A>::add(acc[0], first);
-        emit_advance();  // cur0 -> cur0 + 1
+        A t = acc[0];
+#pragma unroll
+        for (int k = 1; k < W; ++k) t = Op<A>::add(t, acc[k]);
+        t = warp_reduce(t);
+        if (lane == 0) seg_out(p, cur0, Op<A>::add(t, first));
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = Op<A>::zero();
         // step over the segments emitted above to the one open at the row's end
         cur = cur0 + m;
         cur_start = last_pos;
@@ -457,13 +464,15 @@ __global__ void __launch_bounds__(256) seg_finish_kernel(const SegParams p, int6
     finish_span<A>(p, s, w, (end - 1 - base) / E, lane);
 }
 
+// The dense variant exists for at most 4 rows in flight per warp: with 8 its
+// larger state through the hot loop cost 20-65 % on sparse layouts.
 template <int DT, bool COMP, int VB, bool DENSE>
 inline const void* pick_seg(int unroll) {
     switch (unroll) {
     case 1: return (const void*)seg_kernel<DT, COMP, VB, 1, DENSE>;
     case 2: return (const void*)seg_kernel<DT, COMP, VB, 2, DENSE>;
     case 4: return (const void*)seg_kernel<DT, COMP, VB, 4, DENSE>;
-    case 8: return (const void*)seg_kernel<DT, COMP, VB, 8, DENSE>;
+    case 8: return DENSE ? nullptr : (const void*)seg_kernel<DT, COMP, VB, 8, false>;
     default: return nullptr;
     }
 }
