@@ -376,7 +376,8 @@ def seglayouts_suite(args):
     """The segmented kernel across layouts at ~2^28 FP32 elements: 10,000 and
     100,000 lognormal segments, 1M / 4M / 16M equal ones (268, 64 and 16
     elements), 4M lognormal short ones (median 40, empty ones included); the
-    default kernel and SR_F_DENSE_SEGMENTS, two launch shapes, atomic finish;
+    default kernel and SR_F_DENSE_SEGMENTS in two launch shapes, and the TMA
+    form (SR_F_BULK, 256 threads, chunks of 4 rows, 2 stages); atomic finish;
     device time per call in a CUDA graph."""
     import torch
     import paper_2004_05371_gb300 as sr
@@ -399,20 +400,23 @@ def seglayouts_suite(args):
             raise RuntimeError("layout %s needs %d elements, buffer holds %d" % (name, n, NX))
         od = torch.from_numpy(off).cuda()
         out = torch.empty(nseg, dtype=torch.float32, device="cuda")
-        for shape in ((256, 32, 8), (512, 32, 4)):
-            for dense in (0, sr.F_DENSE_SEGMENTS):
-                cfg = sr.make_config(sr.ATOMIC | dense, block_threads=shape[0], vec_bytes=shape[1], unroll=shape[2])
+        for shape, flags in (((256, 32, 8), 0), ((256, 32, 8), sr.F_DENSE_SEGMENTS), ((512, 32, 4), 0),
+                             ((512, 32, 4), sr.F_DENSE_SEGMENTS), ((256, 32, 4), sr.F_BULK)):
+            cfg = sr.make_config(sr.ATOMIC | flags, block_threads=shape[0], vec_bytes=shape[1], unroll=shape[2],
+                                 stages=2 if flags == sr.F_BULK else 0)
 
-                def call(cfg=cfg):
-                    sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(),
-                                                         cfg, torch.cuda.current_stream().cuda_stream))
-                ms = _graph_time(torch, s, call, 5, reps=4)
-                r = sr.plan_segmented(nseg, sr.F32, cfg)  # the shape that ran (dense lowers unroll 8 to 4)
-                _emit({"suite": "seglayouts", "layout": name, "nseg": nseg, "n": n, "dense": bool(dense),
-                       "shape": "%d threads x %d B x unroll %d" % shape,
-                       "ran": "%d threads x %d B x unroll %d" % (r.block_threads, r.vec_bytes, r.unroll),
-                       "us": round(ms * 1e3, 2),
-                       "gbs": round(n * 4 / (ms * 1e-3) / 1e9, 1)})
+            def call(cfg=cfg):
+                sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(),
+                                                     cfg, torch.cuda.current_stream().cuda_stream))
+            ms = _graph_time(torch, s, call, 5, reps=4)
+            r = sr.plan_segmented(nseg, sr.F32, cfg)  # the shape that ran (dense lowers unroll 8 to 4)
+            _emit({"suite": "seglayouts", "layout": name, "nseg": nseg, "n": n,
+                   "dense": bool(flags & sr.F_DENSE_SEGMENTS), "bulk": bool(flags & sr.F_BULK),
+                   "shape": "%d threads x %d B x unroll %d" % shape,
+                   "ran": "%d threads x %d B x unroll %d%s" % (r.block_threads, r.vec_bytes, r.unroll,
+                                                               ", %d stages" % r.stages if r.stages else ""),
+                   "us": round(ms * 1e3, 2),
+                   "gbs": round(n * 4 / (ms * 1e-3) / 1e9, 1)})
         del od, out
         torch.cuda.empty_cache()
     return 0

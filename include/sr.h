@@ -241,10 +241,19 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * finished by the configured grid stage: SR_TWO_KERNEL, SR_GRID_SYNC,
  * SR_LAST_BLOCK (default; per-segment tickets) or SR_ATOMIC (out zeroed
  * first; FP order not deterministic).  All other forms are deterministic.
- * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE),
- * block_threads (at most 512), ctas_per_sm, grid (at most 65536 warps in
- * total), vec_bytes, unroll, scale (FP8).  SR_SINGLE_CLUSTER, cluster bits and SR_F_BULK ->
- * SR_ERR_UNSUPPORTED.
+ * Load path: rows of 16/32-byte vectors loaded into registers (LDG), or with
+ * SR_F_BULK each warp streams its piece through its own ring of `stages`
+ * (2..8, default 2) chunks of `unroll` rows (2, 4 or 8; default 4) in shared
+ * memory, one cp.async.bulk per chunk (the TMA form; every wait bounded, an
+ * expired one reported as SR_ERR_TIMEOUT by sr_stream_status).  Without an
+ * explicit shape (vec_bytes, unroll, block_threads and stages all 0) calls
+ * with 32768 or more segments take the TMA form, fewer the LDG one.
+ * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE, SR_F_BULK,
+ * SR_F_DENSE_SEGMENTS), block_threads (at most 512), ctas_per_sm, grid (at
+ * most 65536 warps in total), vec_bytes, unroll, stages (TMA form), scale
+ * (FP8).  SR_SINGLE_CLUSTER, cluster bits and SR_F_BULK with
+ * SR_F_DENSE_SEGMENTS -> SR_ERR_UNSUPPORTED; a ring larger than a CTA's
+ * shared memory -> SR_ERR_LAUNCH.
  * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,
  * bad config), SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
 int sr_reduce_sum_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,

@@ -254,11 +254,12 @@ int sr_plan_segmented(int64_t nseg, int dtype, const sr_config* cfg, sr_config* 
     st = seg_plan(nseg, dtype, c, *d, &p);
     if (st != SR_OK) return st;
     sr_config r = c;
-    r.variant = (c.variant & ~SR_STAGE_MASK) | p.stage;
+    r.variant = (c.variant & ~(SR_STAGE_MASK | SR_F_BULK)) | p.stage | (p.bulk ? SR_F_BULK : 0);
     r.block_threads = p.block;
     r.grid = p.grid;
     r.vec_bytes = p.vec;
     r.unroll = p.unroll;
+    r.stages = p.bulk ? p.stages : 0;
     r.scale = p.scale;
     *resolved = r;
     return SR_OK;

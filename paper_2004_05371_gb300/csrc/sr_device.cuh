@@ -307,6 +307,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
         if (global_timer_ns() - t0 > limit_ns) return false;
     }
 }
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// later bulk copies (async proxy) into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 // 1-D bulk copy global -> this CTA's shared memory; completes `bytes`
 // transaction bytes on `bar`.  dst, src 16-byte aligned; bytes % 16 == 0.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {

@@ -63,8 +63,10 @@ struct SegPlan {
     int dtype = 0;
     int64_t nseg = 0;
     int stage = 0;
-    bool comp = false, fp64 = false, dense = false;
+    bool comp = false, fp64 = false, dense = false, bulk = false;
     int vec = 16, unroll = 4, block = 256, grid = 0;
+    int stages = 0;
+    size_t smem = 0;  // dynamic shared memory of the TMA form
     int64_t warps = 0;
     float scale = 1.f;
     const void* main = nullptr;

@@ -46,13 +46,15 @@ struct SegParams {
     float scale;
     int stage;
     int fp64;
+    int stages;                 // TMA form: ring stages per warp
+    uint64_t limit_ns;          // TMA form: bound of every mbarrier wait
 };
 
 // Per-dtype segmented kernel selection.
-bool seg_kernels_f32(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
-bool seg_kernels_i32(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
-bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
-bool seg_kernels_fp8(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin);
+bool seg_kernels_f32(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
+bool seg_kernels_i32(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
+bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
+bool seg_kernels_fp8(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
 
 struct KernelSet {
     const void* main = nullptr;   // thread..grid stages

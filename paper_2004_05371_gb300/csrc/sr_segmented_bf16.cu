@@ -2,8 +2,8 @@
 #include "sr_segmented_kernels.cuh"
 
 namespace sr {
-bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, const void** main, const void** fin) {
-    return comp ? pick_seg_kernels<kDtBF16, true>(vec, unroll, dense, main, fin)
-                : pick_seg_kernels<kDtBF16, false>(vec, unroll, dense, main, fin);
+bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin) {
+    return comp ? pick_seg_kernels<kDtBF16, true>(vec, unroll, dense, bulk, main, fin)
+                : pick_seg_kernels<kDtBF16, false>(vec, unroll, dense, bulk, main, fin);
 }
 }  // namespace sr

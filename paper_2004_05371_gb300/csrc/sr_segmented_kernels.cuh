@@ -180,7 +180,12 @@ template <class A> __device__ __forceinline__ void span_arrive(const SegParams& 
 // boundary.
 constexpr int kScanMin = 3;  // boundaries in a row from which the warp-wide pass pays
 
-template <int DT, bool COMP, int VB, int UNROLL, bool DENSE>
+// BULK: the warp's vector body streams through its own ring of p.stages
+// chunks of UNROLL rows in shared memory, one cp.async.bulk per chunk issued by
+// lane 0 and completing on the chunk stage's mbarrier (every wait bounded by
+// p.limit_ns; on expiry the warp records SR_ERR_TIMEOUT, waits for the copies
+// it issued, and stops).  No registers hold rows in flight.
+template <int DT, bool COMP, int VB, int UNROLL, bool DENSE, bool BULK>
 __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     using A = typename Acc<DT, COMP>::T;
     constexpr int EB = SegElem<DT>::v;
@@ -211,11 +216,36 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     const unsigned char* body = p.x + a0 * EB;
 
     // first batch of rows in flight before the segment search
-    uint32_t buf[UNROLL][W];
+    uint32_t buf[BULK ? 1 : UNROLL][W];
+    constexpr uint32_t CHUNK = (uint32_t)UNROLL * 32u * VB;  // bytes of one ring stage
+    const int64_t nchunks = (nrows + UNROLL - 1) / UNROLL;
+    uint32_t ring = 0, bars = 0;
+    // lane 0: copy chunk k of the body into its ring stage
+    auto issue = [&](int64_t k) {
+        const int64_t v0 = k * (UNROLL * 32);
+        if (v0 >= nvec) return;
+        const int64_t nv = (nvec - v0 < UNROLL * 32) ? nvec - v0 : (int64_t)UNROLL * 32;
+        const int st = (int)(k % p.stages);
+        mbar_arrive_expect_tx(bars + 8u * st, (uint32_t)(nv * VB));
+        bulk_g2s(ring + (uint32_t)st * CHUNK, body + v0 * VB, (uint32_t)(nv * VB), bars + 8u * st);
+    };
+    if constexpr (BULK) {
+        extern __shared__ __align__(128) unsigned char seg_dsm[];
+        const int wib = threadIdx.x >> 5, nwib = blockDim.x >> 5;
+        ring = smem_u32(seg_dsm) + (uint32_t)(wib * p.stages) * CHUNK;
+        bars = smem_u32(seg_dsm) + (uint32_t)(nwib * p.stages) * CHUNK + (uint32_t)(wib * p.stages) * 8u;
+        if (lane == 0) {
+            for (int st = 0; st < p.stages; ++st) mbar_init(bars + 8u * st, 1);
+            mbar_fence_init();
+            for (int64_t k = 0; k < p.stages && k < nchunks; ++k) issue(k);
+        }
+        __syncwarp();
+    } else {
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) {
-        const int64_t v = (int64_t)u * 32 + lane;
-        if (v < nvec) ldg_vec(body + v * VB, buf[u]);
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t v = (int64_t)u * 32 + lane;
+            if (v < nvec) ldg_vec(body + v * VB, buf[u]);
+        }
     }
 
     const int64_t s_begin = warp_lower_bound(p.offsets, p.nseg, base + w * E, lane);
@@ -410,22 +440,67 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     };
 
     scalar_chunk(lo, a0);
-    for (int64_t r = 0; r < nrows; r += UNROLL) {
-        if (r > 0) {
+    bool bail = false;
+    if constexpr (BULK) {
+        for (int64_t k = 0; k < nchunks; ++k) {
+            const int st = (int)(k % p.stages);
+            const uint32_t par = (uint32_t)((k / p.stages) & 1);
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars + 8u * st, par, p.limit_ns))) {
+                if (lane == 0) {
+                    atomicOr(p.err, kErrTimeout);
+                    // leave no copy writing this CTA's shared memory: wait for the ones
+                    // issued (chunks k .. k + stages - 1), bounded separately (>= 1 s)
+                    const uint64_t drain = p.limit_ns > 1000000000ull ? p.limit_ns : 1000000000ull;
+                    for (int64_t j = k; j < nchunks && j < k + p.stages; ++j)
+                        mbar_wait_bounded(bars + 8u * (uint32_t)(j % p.stages), (uint32_t)((j / p.stages) & 1), drain);
+                }
+                bail = true;
+                break;
+            }
+            const uint32_t sb = ring + (uint32_t)st * CHUNK + (uint32_t)lane * VB;
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                const int64_t v = (r + u) * 32 + lane;
-                if (v < nvec) ldg_vec(body + v * VB, buf[u]);
+                const int64_t r = k * UNROLL + u;
+                if (r < nrows) {
+                    uint32_t words[W];
+#pragma unroll
+                    for (int h = 0; h < W / 4; ++h) {
+                        uint32_t t4[4];
+                        lds_vec(sb + (uint32_t)u * 32u * VB + 16u * h, t4);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) words[4 * h + i] = t4[i];
+                    }
+                    row(r, words);
+                }
+            }
+            __syncwarp();  // every lane has read the stage
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(k + p.stages);
             }
         }
+    } else {
+        for (int64_t r = 0; r < nrows; r += UNROLL) {
+            if (r > 0) {
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u)
-            if (r + u < nrows) row(r + u, buf[u]);
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int64_t v = (r + u) * 32 + lane;
+                    if (v < nvec) ldg_vec(body + v * VB, buf[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+                if (r + u < nrows) row(r + u, buf[u]);
+        }
     }
-    scalar_chunk(hi_al, hi);
-    // the segment holding the piece's last element, then any (empty) segment
-    // this warp owns that starts at or after hi
-    while (cur < p.nseg && cur_start < next_lo) emit_advance();
+    if (!bail) {
+        scalar_chunk(hi_al, hi);
+        // the segment holding the piece's last element, then any (empty) segment
+        // this warp owns that starts at or after hi
+        while (cur < p.nseg && cur_start < next_lo) emit_advance();
+    } else {
+        spanning = -1;  // results are void (SR_ERR_TIMEOUT); nothing left to finish
+    }
 
     if (p.stage == kStageTwoKernel || p.stage == kStageGridSync) {
         if (lane == 0) p.last_seg[w] = spanning;
@@ -469,10 +544,20 @@ __global__ void __launch_bounds__(256) seg_finish_kernel(const SegParams p, int6
 template <int DT, bool COMP, int VB, bool DENSE>
 inline const void* pick_seg(int unroll) {
     switch (unroll) {
-    case 1: return (const void*)seg_kernel<DT, COMP, VB, 1, DENSE>;
-    case 2: return (const void*)seg_kernel<DT, COMP, VB, 2, DENSE>;
-    case 4: return (const void*)seg_kernel<DT, COMP, VB, 4, DENSE>;
-    case 8: return DENSE ? nullptr : (const void*)seg_kernel<DT, COMP, VB, 8, false>;
+    case 1: return (const void*)seg_kernel<DT, COMP, VB, 1, DENSE, false>;
+    case 2: return (const void*)seg_kernel<DT, COMP, VB, 2, DENSE, false>;
+    case 4: return (const void*)seg_kernel<DT, COMP, VB, 4, DENSE, false>;
+    case 8: return DENSE ? nullptr : (const void*)seg_kernel<DT, COMP, VB, 8, false, false>;
+    default: return nullptr;
+    }
+}
+// The TMA form: chunks of 2, 4 or 8 rows, no dense pass.
+template <int DT, bool COMP, int VB>
+inline const void* pick_seg_bulk(int unroll) {
+    switch (unroll) {
+    case 2: return (const void*)seg_kernel<DT, COMP, VB, 2, false, true>;
+    case 4: return (const void*)seg_kernel<DT, COMP, VB, 4, false, true>;
+    case 8: return (const void*)seg_kernel<DT, COMP, VB, 8, false, true>;
     default: return nullptr;
     }
 }
@@ -484,8 +569,13 @@ inline const void* pick_seg_vec(int vec, int unroll) {
 }
 
 template <int DT, bool COMP>
-inline bool pick_seg_kernels(int vec, int unroll, bool dense, const void** main, const void** fin) {
-    *main = dense ? pick_seg_vec<DT, COMP, true>(vec, unroll) : pick_seg_vec<DT, COMP, false>(vec, unroll);
+inline bool pick_seg_kernels(int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin) {
+    if (bulk)
+        *main = dense ? nullptr
+                      : (vec == 16 ? pick_seg_bulk<DT, COMP, 16>(unroll)
+                                   : (vec == 32 ? pick_seg_bulk<DT, COMP, 32>(unroll) : nullptr));
+    else
+        *main = dense ? pick_seg_vec<DT, COMP, true>(vec, unroll) : pick_seg_vec<DT, COMP, false>(vec, unroll);
     *fin = (const void*)seg_finish_kernel<DT, COMP>;
     return *main != nullptr;
 }

@@ -95,7 +95,9 @@ def test_segmented_rejects_bad_arguments_without_gpu(lib):
     assert call(off=ALIGNED + 4) == sr.ERR_ARG                     # offsets need 8-byte alignment
     assert call(dtype=sr.I32, out=ALIGNED + 4) == sr.ERR_ARG       # int64 results need 8 bytes
     assert call(variant=sr.SINGLE_CLUSTER) == sr.ERR_UNSUPPORTED
-    assert call(variant=sr.LAST_BLOCK | sr.F_BULK) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.F_BULK | sr.F_DENSE_SEGMENTS) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.F_BULK, unroll=1) == sr.ERR_ARG     # TMA chunks: 2, 4 or 8 rows
+    assert call(variant=sr.LAST_BLOCK | sr.F_BULK, stages=9) == sr.ERR_ARG
     assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1)) == sr.ERR_UNSUPPORTED
     assert call(block_threads=100) == sr.ERR_ARG
     assert call(grid=100000, block_threads=512) == sr.ERR_ARG      # more than 65536 warps

@@ -247,3 +247,68 @@ def test_many_small_lognormal_segments(sr, stage):
             exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
             sabs = oracle.sum_e4m3(codes[a:b] & 0x7F, deq)
             assert abs(got[s] - exs) <= 4 * EPS32 * sabs * 1.001 + 1e-30, (dense, s)
+
+
+BULK = 0x400  # SR_F_BULK: each warp streams its piece through a TMA ring in shared memory
+
+
+@pytest.mark.parametrize("stage", STAGES)
+@pytest.mark.parametrize("vec,unroll,stages,block", [(32, 4, 3, 256), (32, 2, 2, 64), (32, 8, 2, 256),
+                                                     (16, 4, 4, 128), (16, 8, 3, 256), (32, 4, 8, 32)])
+def test_bulk_ring(sr, stage, vec, unroll, stages, block):
+    """The TMA form of the segmented kernel: random layouts with empty, tiny and
+    long segments, aligned and misaligned data, every grid stage and ring
+    shape; bit-exact for int32, within the gates for binary32 (plain and
+    compensated)."""
+    for nseg, max_len in ((1, 100_000), (33, 7), (5000, 40), (300, 20_000)):
+        off = workloads.random_segment_offsets(nseg, max_len, seed=nseg + max_len + unroll)
+        n = int(off[-1])
+        xi = workloads.uniform_i32(n, seed=7)
+        xf = workloads.uniform_f32(n, seed=7)
+        for x_off in (0, 1):
+            cfg = dict(vec_bytes=vec, unroll=unroll, stages=stages, block_threads=block)
+            _check(sr, xi, off, stage | BULK, x_off, **cfg)
+            _check(sr, xf, off, stage | BULK, x_off, **cfg)
+        _check(sr, xf, off, stage | BULK | 0x100, **cfg)
+
+
+def test_bulk_ring_dtypes_and_plan(sr):
+    off = workloads.segment_offsets(2000, 1 << 21, seed=13, median=512, sigma=2.0, hi=1 << 19)
+    n = int(off[-1])
+    x = workloads.lognormal_f32(n, seed=13, sigma=2.0)
+    bits = workloads.to_bf16_bits(x)
+    dec_b = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+    codes, deq = workloads.to_e4m3_codes(x)
+    od = torch.from_numpy(off).cuda()
+    xd_b = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    xd_f = torch.from_numpy(codes).cuda()
+    for st in STAGES:
+        got = sr.reduce_sum_segmented(xd_b, od, variant=st | BULK).cpu().numpy()
+        assert np.all(np.abs(got - oracle.segexact_f32(dec_b, off)) <=
+                      4 * EPS32 * oracle.segsum_abs_f32(dec_b, off) + 1e-30)
+        got = sr.reduce_sum_segmented(xd_f, od, config=sr.make_config(st | BULK, scale=deq)).cpu().numpy()
+        for s in range(0, 2000, 97):
+            a, b = off[s], off[s + 1]
+            exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
+            assert abs(got[s] - exs) <= 4 * EPS32 * oracle.sum_e4m3(codes[a:b] & 0x7F, deq) * 1.001 + 1e-30
+    r = sr.plan_segmented(2000, sr.F32, sr.make_config(sr.LAST_BLOCK | BULK))
+    assert r.variant & BULK and r.unroll == 4 and r.stages == 2
+    with pytest.raises(sr.SRError):   # the TMA form has no dense pass
+        sr.plan_segmented(2000, sr.F32, sr.make_config(sr.LAST_BLOCK | BULK | DENSE))
+    with pytest.raises(sr.SRError) as e:  # 16 warps x 2 stages x 8 KiB: more shared memory than a CTA has
+        sr.plan_segmented(2000, sr.F32, sr.make_config(sr.LAST_BLOCK | BULK, block_threads=512, unroll=8, stages=2))
+    assert e.value.status == sr.ERR_LAUNCH
+
+
+def test_default_load_path_by_segment_count(sr):
+    """Without an explicit shape, 32768 or more segments take the TMA form,
+    fewer the LDG one; any explicit shape field keeps the LDG path."""
+    assert sr.plan_segmented(32767, sr.F32).variant & BULK == 0
+    r = sr.plan_segmented(32768, sr.F32)
+    assert r.variant & BULK and (r.unroll, r.stages) == (4, 2)
+    assert sr.plan_segmented(100_000, sr.F32, sr.make_config(sr.ATOMIC, unroll=8)).variant & BULK == 0
+    off = workloads.segment_offsets(40_000, 1 << 22, seed=14, median=100, sigma=1.5, lo=0, hi=1 << 16)
+    n = int(off[-1])
+    for st in STAGES:
+        _check(sr, workloads.uniform_i32(n, seed=14), off, st)
+        _check(sr, workloads.uniform_f32(n, seed=14), off, st, 1)
