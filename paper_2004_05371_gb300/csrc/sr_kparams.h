@@ -32,30 +32,6 @@ struct KParams {
     uint64_t limit_ns;        // bound on every device-side wait
 };
 
-// Kernel argument block of the segmented sum (sr_segmented_kernels.cuh).
-struct SegParams {
-    const unsigned char* x;
-    const int64_t* offsets;     // nseg + 1 entries, non-decreasing
-    int64_t nseg;
-    void* out;                  // nseg results
-    unsigned char* carry_first; // W slots of 16 bytes (W = warps of the grid)
-    unsigned char* carry_last;  // W slots of 16 bytes
-    int64_t* last_seg;          // W entries: owned spanning segment or -1
-    unsigned int* cnt;          // W self-resetting tickets (last-block form)
-    int* err;
-    float scale;
-    int stage;
-    int fp64;
-    int stages;                 // TMA form: ring stages per warp
-    uint64_t limit_ns;          // TMA form: bound of every mbarrier wait
-};
-
-// Per-dtype segmented kernel selection.
-bool seg_kernels_f32(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-bool seg_kernels_i32(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-bool seg_kernels_fp8(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-
 struct KernelSet {
     const void* main = nullptr;   // thread..grid stages
     const void* final = nullptr;  // second kernel of the two-kernel form

@@ -4,6 +4,7 @@
 
 #include "sr_internal.h"
 #include "sr_kparams.h"
+#include "sr_segparams.h"
 
 namespace sr {
 

@@ -24,6 +24,7 @@
 
 #include "sr_device.cuh"
 #include "sr_kparams.h"
+#include "sr_segparams.h"
 
 namespace sr {
 
