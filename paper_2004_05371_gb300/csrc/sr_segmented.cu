@@ -14,13 +14,20 @@ constexpr int64_t kSegBulkMin = 32768;  // segments from which the default shape
 
 bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, bool bulk, const void** main,
                  const void** fin) {
+    const void* (*ldg)(bool, int, int, const void**) = nullptr;
+    const void* (*den)(bool, int, int) = nullptr;
+    const void* (*tma)(bool, int, int) = nullptr;
     switch (dtype) {
-    case SR_F32: return seg_kernels_f32(comp, vec, unroll, dense, bulk, main, fin);
-    case SR_I32: return seg_kernels_i32(comp, vec, unroll, dense, bulk, main, fin);
-    case SR_BF16: return seg_kernels_bf16(comp, vec, unroll, dense, bulk, main, fin);
-    case SR_FP8E4M3: return seg_kernels_fp8(comp, vec, unroll, dense, bulk, main, fin);
+    case SR_F32: ldg = seg_ldg_f32; den = seg_dense_f32; tma = seg_tma_f32; break;
+    case SR_I32: ldg = seg_ldg_i32; den = seg_dense_i32; tma = seg_tma_i32; break;
+    case SR_BF16: ldg = seg_ldg_bf16; den = seg_dense_bf16; tma = seg_tma_bf16; break;
+    case SR_FP8E4M3: ldg = seg_ldg_fp8; den = seg_dense_fp8; tma = seg_tma_fp8; break;
     default: return false;
     }
+    const void* plain = ldg(comp, vec, unroll, fin);  // also sets the second kernel
+    if (bulk) *main = dense ? nullptr : tma(comp, vec, unroll);
+    else *main = dense ? den(comp, vec, unroll) : plain;
+    return *main != nullptr;
 }
 }  // namespace
 

@@ -1,9 +1,10 @@
-// Segmented-sum kernel instantiations for one input dtype.
+// Segmented-sum kernels for one input dtype: the LDG form and the second
+// kernel of the two-kernel finish.
 #include "sr_segmented_kernels.cuh"
 
 namespace sr {
-bool seg_kernels_fp8(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin) {
-    return comp ? pick_seg_kernels<kDtFP8, true>(vec, unroll, dense, bulk, main, fin)
-                : pick_seg_kernels<kDtFP8, false>(vec, unroll, dense, bulk, main, fin);
+const void* seg_ldg_fp8(bool comp, int vec, int unroll, const void** fin) {
+    *fin = comp ? (const void*)seg_finish_kernel<kDtFP8, true> : (const void*)seg_finish_kernel<kDtFP8, false>;
+    return comp ? pick_seg_ldg<kDtFP8, true>(vec, unroll) : pick_seg_ldg<kDtFP8, false>(vec, unroll);
 }
 }  // namespace sr

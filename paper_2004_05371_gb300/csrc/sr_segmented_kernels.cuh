@@ -569,16 +569,16 @@ inline const void* pick_seg_vec(int vec, int unroll) {
                      : (vec == 32 ? pick_seg<DT, COMP, 32, DENSE>(unroll) : nullptr);
 }
 
+// The three kernel families of one dtype are instantiated in three
+// translation units (sr_segmented_<dtype>{,_dense,_bulk}.cu) so they compile
+// in parallel.
 template <int DT, bool COMP>
-inline bool pick_seg_kernels(int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin) {
-    if (bulk)
-        *main = dense ? nullptr
-                      : (vec == 16 ? pick_seg_bulk<DT, COMP, 16>(unroll)
-                                   : (vec == 32 ? pick_seg_bulk<DT, COMP, 32>(unroll) : nullptr));
-    else
-        *main = dense ? pick_seg_vec<DT, COMP, true>(vec, unroll) : pick_seg_vec<DT, COMP, false>(vec, unroll);
-    *fin = (const void*)seg_finish_kernel<DT, COMP>;
-    return *main != nullptr;
+inline const void* pick_seg_ldg(int vec, int unroll) { return pick_seg_vec<DT, COMP, false>(vec, unroll); }
+template <int DT, bool COMP>
+inline const void* pick_seg_dense(int vec, int unroll) { return pick_seg_vec<DT, COMP, true>(vec, unroll); }
+template <int DT, bool COMP>
+inline const void* pick_seg_tma(int vec, int unroll) {
+    return vec == 16 ? pick_seg_bulk<DT, COMP, 16>(unroll) : (vec == 32 ? pick_seg_bulk<DT, COMP, 32>(unroll) : nullptr);
 }
 
 }  // namespace sr

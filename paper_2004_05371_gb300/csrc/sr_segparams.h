@@ -25,10 +25,20 @@ struct SegParams {
     uint64_t limit_ns;          // TMA form: bound of every mbarrier wait
 };
 
-// Per-dtype segmented kernel selection.
-bool seg_kernels_f32(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-bool seg_kernels_i32(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-bool seg_kernels_bf16(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
-bool seg_kernels_fp8(bool comp, int vec, int unroll, bool dense, bool bulk, const void** main, const void** fin);
+// Per-dtype segmented kernel selection, one function per kernel family and
+// dtype (each in its own translation unit): the LDG form (which also returns
+// the two-kernel form's second kernel), the dense variant, the TMA form.
+const void* seg_ldg_f32(bool comp, int vec, int unroll, const void** fin);
+const void* seg_dense_f32(bool comp, int vec, int unroll);
+const void* seg_tma_f32(bool comp, int vec, int unroll);
+const void* seg_ldg_i32(bool comp, int vec, int unroll, const void** fin);
+const void* seg_dense_i32(bool comp, int vec, int unroll);
+const void* seg_tma_i32(bool comp, int vec, int unroll);
+const void* seg_ldg_bf16(bool comp, int vec, int unroll, const void** fin);
+const void* seg_dense_bf16(bool comp, int vec, int unroll);
+const void* seg_tma_bf16(bool comp, int vec, int unroll);
+const void* seg_ldg_fp8(bool comp, int vec, int unroll, const void** fin);
+const void* seg_dense_fp8(bool comp, int vec, int unroll);
+const void* seg_tma_fp8(bool comp, int vec, int unroll);
 
 }  // namespace sr
