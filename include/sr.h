@@ -208,7 +208,9 @@ int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out,
 
 /* Synchronise `stream` and report (and clear) device-side error flags raised
  * by this library's kernels on it since the last call: SR_ERR_TIMEOUT when a
- * bounded wait expired, else SR_OK (or SR_ERR_CUDA). */
+ * bounded wait expired, else SR_OK (or SR_ERR_CUDA).  Reporting an error also
+ * clears it and resets the stream's tickets, so the next call starts clean;
+ * results of the calls before it are void. */
 int sr_stream_status(sr_stream_t stream);
 
 /* Synchronise `stream`, then free the library's workspace and host-entry

@@ -368,7 +368,11 @@ int sr_stream_status(sr_stream_t stream) {
     e = cudaMemcpy(&err, ws.err, sizeof err, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return status_from_cuda(e);
     if (err) {
+        // A kernel that gave up may have left tickets half-counted (a segmented
+        // warp that stopped never arrives): start the stream's next call clean.
         e = cudaMemset(ws.err, 0, sizeof err);
+        if (e == cudaSuccess) e = cudaMemset(ws.tickets, 0, 32 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(ws.seg, 0, (size_t)kSegMaxWarps * sizeof(unsigned int));
         if (e != cudaSuccess) return status_from_cuda(e);
     }
     if (err & kErrTimeout) return SR_ERR_TIMEOUT;
