@@ -28,6 +28,14 @@ def test_bounded_wait_times_out_and_context_survives(sr):
         out = sr.reduce_sum(xd, variant=sr.LAST_BLOCK | sr.F_BULK, stream=s)
     s.synchronize()
     assert int(out.item()) == oracle.sum_i32(x)
+    # and so is the segmented path with per-segment tickets (reset with the error)
+    off = workloads.segment_offsets(40_000, 1 << 22, seed=5, median=100, sigma=1.5, lo=0, hi=1 << 16)
+    xs = workloads.uniform_i32(int(off[-1]), seed=5)
+    xsd, od = torch.from_numpy(xs).cuda(), torch.from_numpy(off).cuda()
+    with torch.cuda.stream(s):
+        got = sr.reduce_sum_segmented(xsd, od, variant=sr.LAST_BLOCK, stream=s)   # the TMA form
+    s.synchronize()
+    assert np.array_equal(got.cpu().numpy(), oracle.segsum_i32(xs, off))
     assert sr.stream_status(s) == sr.OK
 
 
