@@ -263,6 +263,19 @@ int sr_reduce_sum_segmented(const void* x, const int64_t* offsets, int64_t nseg,
 int sr_reduce_sum_segmented_ex(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
                                const sr_config* cfg, sr_stream_t stream);
 
+/* The same sum with the offsets checked on the device first: n_elems is the
+ * number of elements x holds (x may be NULL when n_elems == 0).  A small
+ * kernel verifies offsets[0] >= 0, that every offset is >= its predecessor
+ * and offsets[nseg] <= n_elems; if any fails, the summing kernels read
+ * nothing (out is left as it was, or zero for SR_ATOMIC) and the next
+ * sr_stream_status(stream) reports SR_ERR_ARG.  The plain entry points trust
+ * the caller with this contract; this one costs one extra kernel (8 bytes
+ * read per segment).  The paper has no counterpart.  Host-side errors as
+ * sr_reduce_sum_segmented_ex, plus SR_ERR_ARG for n_elems < 0 or x == NULL
+ * with n_elems > 0. */
+int sr_reduce_sum_segmented_checked(const void* x, int64_t n_elems, const int64_t* offsets, int64_t nseg,
+                                    int dtype, void* out, const sr_config* cfg, sr_stream_t stream);
+
 /* Resolved launch shape of a segmented call (as sr_plan).  Needs a device. */
 int sr_plan_segmented(int64_t nseg, int dtype, const sr_config* cfg, sr_config* resolved);
 

@@ -102,6 +102,8 @@ def load():
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     L.sr_reduce_sum.restype = i32
     L.sr_reduce_sum.argtypes = [vp, i64, i32, vp, i32, vp]
+    L.sr_reduce_sum_segmented_checked.restype = i32
+    L.sr_reduce_sum_segmented_checked.argtypes = [vp, i64, vp, i64, i32, vp, ctypes.POINTER(Config), vp]
     L.sr_reduce_sum_ex.restype = i32
     L.sr_reduce_sum_ex.argtypes = [vp, i64, i32, vp, ctypes.POINTER(Config), vp]
     L.sr_reduce_sum_noalloc.restype = i32
@@ -285,6 +287,17 @@ def reduce_sum_segmented_ptr(x_ptr: int, offsets_ptr: int, nseg: int, dtype: int
     return lib().sr_reduce_sum_segmented_ex(ctypes.c_void_p(x_ptr), ctypes.c_void_p(offsets_ptr), int(nseg),
                                             int(dtype), ctypes.c_void_p(out_ptr), cfg,
                                             ctypes.c_void_p(_stream(stream)))
+
+
+def reduce_sum_segmented_checked_ptr(x_ptr: int, n_elems: int, offsets_ptr: int, nseg: int, dtype: int,
+                                     out_ptr: int, config: Config = None, stream=None) -> int:
+    """Raw call of sr_reduce_sum_segmented_checked (offsets validated on the
+    device against n_elems); returns the launch status.  A failed check shows
+    up as SR_ERR_ARG from stream_status()."""
+    cfg = ctypes.byref(config) if config is not None else None
+    return lib().sr_reduce_sum_segmented_checked(ctypes.c_void_p(x_ptr), int(n_elems), ctypes.c_void_p(offsets_ptr),
+                                                 int(nseg), int(dtype), ctypes.c_void_p(out_ptr), cfg,
+                                                 ctypes.c_void_p(_stream(stream)))
 
 
 def reduce_sum_segmented(x, offsets, variant: int = AUTO, out=None, config: Config = None, stream=None,

@@ -113,6 +113,7 @@ int get_workspace(cudaStream_t s, Workspace* ws) {
     w.err = reinterpret_cast<int*>(w.base + 32 * sizeof(unsigned int));  // after 32 tickets
     w.partials = w.base + kHeaderBytes;
     w.seg = w.partials + (size_t)kMaxUnits * kSlotBytes;
+    w.check = reinterpret_cast<int*>(w.base + 160);
     g_workspaces[key] = w;
     *ws = w;
     return SR_OK;
@@ -236,6 +237,26 @@ int sr_reduce_sum_segmented_ex(const void* x, const int64_t* offsets, int64_t ns
     st = get_workspace((cudaStream_t)stream, &ws);
     if (st != SR_OK) return st;
     return seg_launch(x, offsets, out, p, ws, (cudaStream_t)stream);
+}
+
+int sr_reduce_sum_segmented_checked(const void* x, int64_t n_elems, const int64_t* offsets, int64_t nseg,
+                                    int dtype, void* out, const sr_config* cfg, sr_stream_t stream) {
+    const sr_config c = cfg ? *cfg : default_config(SR_AUTO);
+    if (n_elems < 0 || (n_elems > 0 && x == nullptr)) return SR_ERR_ARG;
+    int st = seg_validate(x ? x : offsets, offsets, nseg, dtype, out, c);
+    if (st != SR_OK) return st;
+    if (nseg == 0) return SR_OK;
+    const DeviceInfo* d = current_device(&st);
+    if (!d) return st;
+    SegPlan p;
+    st = seg_plan(nseg, dtype, c, *d, &p);
+    if (st != SR_OK) return st;
+    Workspace ws;
+    st = get_workspace((cudaStream_t)stream, &ws);
+    if (st != SR_OK) return st;
+    st = seg_check(offsets, nseg, n_elems, ws, (cudaStream_t)stream);
+    if (st != SR_OK) return st;
+    return seg_launch(x ? x : offsets, offsets, out, p, ws, (cudaStream_t)stream, /*check=*/true);
 }
 
 int sr_reduce_sum_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
@@ -376,6 +397,7 @@ int sr_stream_status(sr_stream_t stream) {
         if (e != cudaSuccess) return status_from_cuda(e);
     }
     if (err & kErrTimeout) return SR_ERR_TIMEOUT;
+    if (err & kErrBadOffsets) return SR_ERR_ARG;
     if (err) return SR_ERR_LAUNCH;
     return SR_OK;
 }

@@ -29,6 +29,7 @@ struct Workspace {
     int* err = nullptr;
     unsigned char* partials = nullptr;
     unsigned char* seg = nullptr;
+    int* check = nullptr;  // verdict of the checked segmented entry (header byte 160)
 };
 
 struct DeviceInfo {
@@ -106,7 +107,11 @@ int reduce_launch_final(const Plan& p, int units, void* out, const Workspace& ws
 int seg_validate(const void* x, const int64_t* offsets, int64_t nseg, int dtype, const void* out,
                  const sr_config& cfg);
 int seg_plan(int64_t nseg, int dtype, const sr_config& cfg, const DeviceInfo& d, SegPlan* p);
+// Validates offsets (non-decreasing, offsets[0] >= 0, offsets[nseg] <= n_elems)
+// on the device into ws.check and the error word; the next seg_launch with
+// check = true then reads nothing when they fail.
+int seg_check(const int64_t* offsets, int64_t nseg, int64_t n_elems, const Workspace& ws, cudaStream_t s);
 int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& p, const Workspace& ws,
-               cudaStream_t s);
+               cudaStream_t s, bool check = false);
 
 }  // namespace sr

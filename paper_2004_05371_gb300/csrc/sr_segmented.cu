@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "sr_device.cuh"
 #include "sr_internal.h"
 #include "sr_kparams.h"
 #include "sr_segparams.h"
@@ -9,6 +10,23 @@
 namespace sr {
 
 namespace {
+
+// Checked entry: every offset must be >= its predecessor (offsets[0] >= 0)
+// and offsets[nseg] <= n_elems; a violation sets *bad (zeroed just before on
+// the same stream) and the stream's error word.
+__global__ void __launch_bounds__(256) seg_check_kernel(const int64_t* offsets, int64_t nseg, int64_t n_elems,
+                                                        int* bad, int* err) {
+    grid_dependency_wait();
+    allow_dependents();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nseg; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = offsets[i];
+        const bool ok = (i == 0 ? a >= 0 : a >= offsets[i - 1]) && (i < nseg || a <= n_elems);
+        if (!ok) {
+            atomicOr(bad, 1);
+            atomicOr(err, kErrBadOffsets);
+        }
+    }
+}
 constexpr int kKnownSegFlags = SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_DENSE_SEGMENTS | SR_F_BULK;
 constexpr int64_t kSegBulkMin = 32768;  // segments from which the default shape is the TMA form
 
@@ -110,8 +128,28 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     return SR_OK;
 }
 
+int seg_check(const int64_t* offsets, int64_t nseg, int64_t n_elems, const Workspace& ws, cudaStream_t s) {
+    int st = launch_zero(ws.check, sizeof(int), s);
+    if (st != SR_OK) return st;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof lc);
+    lc.gridDim = dim3((unsigned)std::min<int64_t>((nseg + 256) / 256, 1024));
+    lc.blockDim = dim3(256);
+    lc.stream = s;
+    lc.attrs = pdl;
+    lc.numAttrs = 1;
+    int* bad = ws.check;
+    int* err = ws.err;
+    void* args[] = {const_cast<int64_t**>(&offsets), &nseg, &n_elems, &bad, &err};
+    cudaError_t e = cudaLaunchKernelExC(&lc, (const void*)seg_check_kernel, args);
+    return e == cudaSuccess ? SR_OK : status_from_cuda(e);
+}
+
 int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& p, const Workspace& ws,
-               cudaStream_t s) {
+               cudaStream_t s, bool check) {
     SegParams kp;
     std::memset(&kp, 0, sizeof kp);
     kp.x = static_cast<const unsigned char*>(x);
@@ -126,6 +164,7 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
     kp.scale = p.scale;
     kp.stages = p.stages;
     kp.limit_ns = spin_limit_ns();
+    kp.bad = check ? ws.check : nullptr;
     kp.stage = p.stage;
     kp.fp64 = p.fp64 ? 1 : 0;
     cudaError_t e;

@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
     constexpr int RW = 32 * PV;  // elements per row
     grid_dependency_wait();
     allow_dependents();
+    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t Wn = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -526,6 +527,7 @@ __global__ void __launch_bounds__(256) seg_finish_kernel(const SegParams p, int6
     using A = typename Acc<DT, COMP>::T;
     grid_dependency_wait();  // the implicit barrier: every first-kernel warp has finished
     allow_dependents();
+    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= Wn) return;

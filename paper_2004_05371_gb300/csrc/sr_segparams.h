@@ -7,6 +7,8 @@
 
 namespace sr {
 
+constexpr int kErrBadOffsets = 4;  // the checked entry found offsets it may not read with
+
 // Kernel argument block of the segmented sum (sr_segmented_kernels.cuh).
 struct SegParams {
     const unsigned char* x;
@@ -23,6 +25,7 @@ struct SegParams {
     int fp64;
     int stages;                 // TMA form: ring stages per warp
     uint64_t limit_ns;          // TMA form: bound of every mbarrier wait
+    const int* bad;             // checked entry: nonzero = offsets invalid, read nothing (else NULL)
 };
 
 // Per-dtype segmented kernel selection, one function per kernel family and

@@ -120,6 +120,17 @@ def test_differential_latency_host_code_matches_oracle(lib):
     assert lib.sr_differential_latency(arr, 1, arr, 1, 2, 1, ctypes.byref(c), ctypes.byref(c)) == sr.ERR_ARG
 
 
+def test_checked_segmented_rejects_bad_arguments_without_gpu(lib):
+    def call(n_elems=16, x=ALIGNED, nseg=4, **kw):
+        return sr.reduce_sum_segmented_checked_ptr(x, n_elems, ALIGNED, nseg, sr.F32, ALIGNED, sr.make_config(**kw),
+                                                   stream=0)
+    assert call(n_elems=-1) == sr.ERR_ARG
+    assert call(x=0) == sr.ERR_ARG                       # data pointer required when n_elems > 0
+    assert call(nseg=-1) == sr.ERR_ARG
+    assert call(nseg=0) == sr.OK                         # nothing to check, nothing launched
+    assert call(variant=sr.SINGLE_CLUSTER) == sr.ERR_UNSUPPORTED
+
+
 def test_barrier_bench_rejects_bad_config_without_gpu(lib):
     def run(**kw):
         c = sr.BarrierConfig(**kw)

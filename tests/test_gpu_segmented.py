@@ -312,3 +312,46 @@ def test_default_load_path_by_segment_count(sr):
     for st in STAGES:
         _check(sr, workloads.uniform_i32(n, seed=14), off, st)
         _check(sr, workloads.uniform_f32(n, seed=14), off, st, 1)
+
+
+@pytest.mark.parametrize("stage", STAGES)
+@pytest.mark.parametrize("flags", [0, BULK])
+def test_checked_entry(sr, stage, flags):
+    """sr_reduce_sum_segmented_checked: valid offsets give the oracle's sums;
+    offsets past the declared element count, a decreasing pair or a negative
+    first offset make the kernels read nothing and stream_status report
+    SR_ERR_ARG, after which the stream works again.  The declared array sits
+    inside padding, so even an unchecked read of these offsets stays in bounds."""
+    n, nseg, pad = 200_000, 3000, 4096
+    rng = np.random.default_rng(16)
+    good = np.concatenate([[0], np.sort(rng.integers(0, n, nseg - 1)), [n]]).astype(np.int64)
+    x = workloads.uniform_i32(n, seed=16)
+    buf = torch.zeros(n + 2 * pad, dtype=torch.int32, device="cuda")
+    buf[pad:pad + n] = torch.from_numpy(x).cuda()
+    xd = buf[pad:pad + n]
+    out = torch.empty(nseg, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    cfg = sr.make_config(stage | flags)
+
+    def run(off):
+        od = torch.from_numpy(off).cuda()
+        out.fill_(-7)
+        torch.cuda.synchronize()
+        sr.check(sr.reduce_sum_segmented_checked_ptr(xd.data_ptr(), n, od.data_ptr(), nseg, sr.I32, out.data_ptr(),
+                                                     cfg, s))
+        s.synchronize()
+        return sr.stream_status(s), out.cpu().numpy()
+    st, got = run(good)
+    assert st == sr.OK and np.array_equal(got, oracle.segsum_i32(x, good))
+    past = good.copy()
+    past[-1] = n + 1000                     # beyond the declared n, inside the padding
+    swapped = good.copy()
+    swapped[100], swapped[101] = good[101] + 1, good[100]   # a decreasing pair
+    negative = good.copy()
+    negative[0] = -8                        # before the array, inside the padding
+    for bad in (past, swapped, negative):
+        st, got = run(bad)
+        assert st == sr.ERR_ARG
+        assert np.all(got == (0 if stage == sr.ATOMIC else -7))   # nothing summed
+    st, got = run(good)
+    assert st == sr.OK and np.array_equal(got, oracle.segsum_i32(x, good))
