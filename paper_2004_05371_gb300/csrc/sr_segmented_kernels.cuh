@@ -68,6 +68,28 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int64_t* off, int64_t 
 
 // Element j of a vector held as 32-bit words (the masked slow path; j is a
 // compile-time constant after unrolling).
+// Bits j of a PV-bit mask with a <= j < b (a and b clamped to [0, PV]).
+template <int PV> __device__ __forceinline__ uint32_t run_mask(int64_t a, int64_t b) {
+    const int ja = a <= 0 ? 0 : (a >= PV ? PV : (int)a);
+    const int jb = b <= 0 ? 0 : (b >= PV ? PV : (int)b);
+    const uint32_t below_b = jb >= 32 ? 0xffffffffu : (1u << jb) - 1u;
+    const uint32_t below_a = ja >= 32 ? 0xffffffffu : (1u << ja) - 1u;
+    return below_b & ~below_a;
+}
+
+// Sum of a lane's W word accumulators as a pairwise tree (log2 W dependent adds).
+template <class A, int W> __device__ __forceinline__ A sum_words(const A (&acc)[W]) {
+    A t[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) t[k] = acc[k];
+#pragma unroll
+    for (int h = 1; h < W; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k + h < W; k += 2 * h) t[k] = Op<A>::add(t[k], t[k + h]);
+    }
+    return t[0];
+}
+
 template <int DT, class A> __device__ __forceinline__ void acc_vec_elem(A& a, const uint32_t* r, int j);
 template <> __device__ __forceinline__ void acc_vec_elem<kDtI32, long long>(long long& a, const uint32_t* r, int j) {
     a += (long long)(int)r[j];
@@ -187,7 +209,7 @@ constexpr int kScanMin = 3;  // boundaries in a row from which the warp-wide pas
 // p.limit_ns; on expiry the warp records SR_ERR_TIMEOUT, waits for the copies
 // it issued, and stops).  No registers hold rows in flight.
 template <int DT, bool COMP, int VB, int UNROLL, bool DENSE, bool BULK>
-__global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
+__global__ void __launch_bounds__(512, 1) seg_kernel(const SegParams p) {
     using A = typename Acc<DT, COMP>::T;
     constexpr int EB = SegElem<DT>::v;
     constexpr int PV = VB / EB;  // elements per lane vector
@@ -265,10 +287,7 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
 
     // emit the current segment's piece and move to the next segment
     auto emit_advance = [&]() {
-        A t = acc[0];
-#pragma unroll
-        for (int k = 1; k < W; ++k) t = Op<A>::add(t, acc[k]);
-        A v = warp_reduce(t);
+        A v = warp_reduce(sum_words<A, W>(acc));
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = Op<A>::zero();
         const int64_t s = cur;
@@ -335,9 +354,10 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
         const int q = has_b ? (int)(bpos - e0) : PV;  // elements j < q precede the boundary
         A head = Op<A>::zero(), tail = Op<A>::zero();
         if (valid) {
+            const int jv = (c1 - e0 < PV) ? (int)(c1 - e0) : PV;  // elements of the lane inside the row
 #pragma unroll
             for (int j = 0; j < PV; ++j) {
-                if (e0 + j < c1) {
+                if (j < jv) {
                     if (j < q) acc_vec_elem<DT>(head, r_words, j);
                     else acc_vec_elem<DT>(tail, r_words, j);
                 }
@@ -366,10 +386,7 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
         // segment cur, owned by this warp and complete: the rows before this
         // one (acc, per lane) plus its part of this row
         const A first = Op<A>::shfl(closed, __ffs(tmask) - 1);
-        A t = acc[0];
-#pragma unroll
-        for (int k = 1; k < W; ++k) t = Op<A>::add(t, acc[k]);
-        t = warp_reduce(t);
+        A t = warp_reduce(sum_words<A, W>(acc));
         if (lane == 0) seg_out(p, cur0, Op<A>::add(t, first));
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = Op<A>::zero();
@@ -430,11 +447,12 @@ __global__ void __launch_bounds__(512) seg_kernel(const SegParams p) {
         for (;;) {  // segments end inside this row (one reduction per segment)
             if (valid) {
                 // element j of the lane's vector belongs to the current segment
-                // when cur_start <= e0 + j < cur_end (static indices keep the
-                // vector in registers)
+                // when cur_start <= e0 + j < cur_end: one bit per j, from two
+                // clamped offsets (static indices keep the vector in registers)
+                const uint32_t m = run_mask<PV>(cur_start - e0, cur_end - e0);
 #pragma unroll
                 for (int j = 0; j < PV; ++j)
-                    if (e0 + j >= cur_start && e0 + j < cur_end) acc_vec_elem<DT>(acc[j * W / PV], r_words, j);
+                    if ((m >> j) & 1u) acc_vec_elem<DT>(acc[j * W / PV], r_words, j);
             }
             if (cur_end >= c1) break;
             emit_advance();
