@@ -394,14 +394,22 @@ def seglayouts_suite(args):
              ("16M equal (16)", np.arange(16_777_217, dtype=np.int64) * 16),
              ("4M lognormal (median 40, empties)",
               workloads.segment_offsets(4 << 20, N, seed=3, median=40, sigma=1.5, lo=0, hi=1 << 16))]
+    forms = {"ldg256": ((256, 32, 8), 0), "dense256": ((256, 32, 8), sr.F_DENSE_SEGMENTS),
+             "ldg512": ((512, 32, 4), 0), "dense512": ((512, 32, 4), sr.F_DENSE_SEGMENTS),
+             "tma": ((256, 32, 4), sr.F_BULK)}
+    only = getattr(args, "layout", None)
+    form = getattr(args, "seg_form", None)
     for name, off in cases:
+        if only and only not in name:
+            continue
         nseg, n = len(off) - 1, int(off[-1])
         if n > NX:
             raise RuntimeError("layout %s needs %d elements, buffer holds %d" % (name, n, NX))
         od = torch.from_numpy(off).cuda()
         out = torch.empty(nseg, dtype=torch.float32, device="cuda")
-        for shape, flags in (((256, 32, 8), 0), ((256, 32, 8), sr.F_DENSE_SEGMENTS), ((512, 32, 4), 0),
-                             ((512, 32, 4), sr.F_DENSE_SEGMENTS), ((256, 32, 4), sr.F_BULK)):
+        for key, (shape, flags) in forms.items():
+            if form and key != form:
+                continue
             cfg = sr.make_config(sr.ATOMIC | flags, block_threads=shape[0], vec_bytes=shape[1], unroll=shape[2],
                                  stages=2 if flags == sr.F_BULK else 0)
 
