@@ -376,8 +376,9 @@ def seglayouts_suite(args):
     """The segmented kernel across layouts at ~2^28 FP32 elements: 10,000 and
     100,000 lognormal segments, 1M / 4M / 16M equal ones (268, 64 and 16
     elements), 4M lognormal short ones (median 40, empty ones included); the
-    default kernel and SR_F_DENSE_SEGMENTS in two launch shapes, and the TMA
-    form (SR_F_BULK, 256 threads, chunks of 4 rows, 2 stages); atomic finish;
+    default kernel and SR_F_DENSE_SEGMENTS in two launch shapes, the TMA
+    form (SR_F_BULK, 256 threads, chunks of 4 rows, 2 stages) and the
+    warp-per-segment form (SR_F_WARP_SEGMENTS, 16 B x 4 and 16 B x 2); atomic finish;
     device time per call in a CUDA graph."""
     import torch
     import paper_2004_05371_gb300 as sr
@@ -396,7 +397,8 @@ def seglayouts_suite(args):
               workloads.segment_offsets(4 << 20, N, seed=3, median=40, sigma=1.5, lo=0, hi=1 << 16))]
     forms = {"ldg256": ((256, 32, 8), 0), "dense256": ((256, 32, 8), sr.F_DENSE_SEGMENTS),
              "ldg512": ((512, 32, 4), 0), "dense512": ((512, 32, 4), sr.F_DENSE_SEGMENTS),
-             "tma": ((256, 32, 4), sr.F_BULK)}
+             "tma": ((256, 32, 4), sr.F_BULK), "warp16": ((256, 16, 4), sr.F_WARP_SEGMENTS),
+             "warp16u2": ((256, 16, 2), sr.F_WARP_SEGMENTS)}
     only = getattr(args, "layout", None)
     form = getattr(args, "seg_form", None)
     for name, off in cases:
@@ -411,7 +413,7 @@ def seglayouts_suite(args):
             if form and key != form:
                 continue
             cfg = sr.make_config(sr.ATOMIC | flags, block_threads=shape[0], vec_bytes=shape[1], unroll=shape[2],
-                                 stages=2 if flags == sr.F_BULK else 0)
+                                 stages=2 if flags & sr.F_BULK else 0)
 
             def call(cfg=cfg):
                 sr.check(sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(),
@@ -420,6 +422,7 @@ def seglayouts_suite(args):
             r = sr.plan_segmented(nseg, sr.F32, cfg)  # the shape that ran (dense lowers unroll 8 to 4)
             _emit({"suite": "seglayouts", "layout": name, "nseg": nseg, "n": n,
                    "dense": bool(flags & sr.F_DENSE_SEGMENTS), "bulk": bool(flags & sr.F_BULK),
+                   "warp": bool(flags & sr.F_WARP_SEGMENTS),
                    "shape": "%d threads x %d B x unroll %d" % shape,
                    "ran": "%d threads x %d B x unroll %d%s" % (r.block_threads, r.vec_bytes, r.unroll,
                                                                ", %d stages" % r.stages if r.stages else ""),

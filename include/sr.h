@@ -100,6 +100,19 @@ typedef enum {
                                    qualify.  512-thread CTAs by default; runs at most 4 rows in
                                    flight per warp (unroll 8 is lowered to 4; sr_plan_
                                    segmented reports it).  Same results contract. */
+#define SR_F_WARP_SEGMENTS 0x4000 /* segmented only: each warp sums whole segments
+                                   (blocks of up to 32 consecutive segments per warp,
+                                   one coalesced offsets load per block, one warp
+                                   reduction and one store per segment).  No segment
+                                   crosses a warp, so the grid stage is not used and
+                                   nothing is zeroed or finished; deterministic.  For
+                                   many segments of similar length: a long segment is
+                                   summed by one warp alone.  Segments go in pairs,
+                                   both first batches of loads in flight together; a
+                                   batch is `unroll` 16/32-byte vectors per lane
+                                   (default 16 bytes x 2; unroll 1/2/4/8).  Not with
+                                   SR_F_BULK or SR_F_DENSE_SEGMENTS
+                                   (SR_ERR_UNSUPPORTED). */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses
@@ -250,11 +263,13 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * expired one reported as SR_ERR_TIMEOUT by sr_stream_status).  Without an
  * explicit shape (vec_bytes, unroll, block_threads and stages all 0) calls
  * with 32768 or more segments take the TMA form, fewer the LDG one.
+ * With SR_F_WARP_SEGMENTS whole segments go to single warps instead (see the
+ * flag).
  * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE, SR_F_BULK,
- * SR_F_DENSE_SEGMENTS), block_threads (at most 512), ctas_per_sm, grid (at
+ * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS), block_threads (at most 512), ctas_per_sm, grid (at
  * most 65536 warps in total), vec_bytes, unroll, stages (TMA form), scale
- * (FP8).  SR_SINGLE_CLUSTER, cluster bits and SR_F_BULK with
- * SR_F_DENSE_SEGMENTS -> SR_ERR_UNSUPPORTED; a ring larger than a CTA's
+ * (FP8).  SR_SINGLE_CLUSTER, cluster bits, and any two of SR_F_BULK,
+ * SR_F_DENSE_SEGMENTS and SR_F_WARP_SEGMENTS -> SR_ERR_UNSUPPORTED; a ring larger than a CTA's
  * shared memory -> SR_ERR_LAUNCH.
  * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,
  * bad config), SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
@@ -267,7 +282,8 @@ int sr_reduce_sum_segmented_ex(const void* x, const int64_t* offsets, int64_t ns
  * number of elements x holds (x may be NULL when n_elems == 0).  A small
  * kernel verifies offsets[0] >= 0, that every offset is >= its predecessor
  * and offsets[nseg] <= n_elems; if any fails, the summing kernels read
- * nothing (out is left as it was, or zero for SR_ATOMIC) and the next
+ * nothing (out is left as it was, or zero for SR_ATOMIC without
+ * SR_F_WARP_SEGMENTS) and the next
  * sr_stream_status(stream) reports SR_ERR_ARG.  The plain entry points trust
  * the caller with this contract; this one costs one extra kernel (8 bytes
  * read per segment).  The paper has no counterpart.  Host-side errors as
@@ -451,10 +467,23 @@ int sr_selector_choose(sr_selector selector, int64_t n, int dtype, int64_t nseg,
  * (memoised; that first call synchronises `stream`).  Other arguments and
  * errors as sr_reduce_sum_ex / sr_reduce_sum_segmented_ex; the segmented form
  * takes the segment-length statistics from the caller (n = mean * nseg) and
- * adds SR_F_DENSE_SEGMENTS to the chosen configuration when segments are
- * uniformly short (mean * element size <= 512 bytes and std <= mean / 2). */
+ * applies the form sr_segmented_layout_flags gives for them: it adds
+ * SR_F_DENSE_SEGMENTS to the chosen configuration, or replaces the chosen
+ * configuration's shape with SR_F_WARP_SEGMENTS at its default shape. */
 int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int dtype, void* out,
                            sr_stream_t stream);
+/* The segmented form for a layout, from the caller's segment-length
+ * statistics (mean, standard deviation, maximum; len_max <= 0 when unknown,
+ * then mean + 4 std stands in) and the device's SM count, in this order:
+ * SR_F_DENSE_SEGMENTS for uniformly very short segments (mean * element size
+ * <= 128 bytes, std <= mean / 2); SR_F_WARP_SEGMENTS for 2^19 or more
+ * segments none longer than twice a warp's even share of the elements
+ * (2 * mean * nseg / (32 * sms)); SR_F_DENSE_SEGMENTS for uniformly short
+ * segments (<= 512 bytes, std <= mean / 2); else 0 (the plain form).
+ * Host-only and pure (no device call).
+ * Returns the flag, or a negated status: -SR_ERR_DTYPE, -SR_ERR_ARG (sms < 1,
+ * nseg < 0, negative or NaN statistics). */
+int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean, double len_std, double len_max);
 int sr_reduce_sum_segmented_selected(sr_selector selector, const void* x, const int64_t* offsets, int64_t nseg,
                                      int dtype, void* out, double len_mean, double len_std, double len_max,
                                      sr_stream_t stream);

@@ -26,6 +26,7 @@ F_BULK = 0x400
 F_HOST_DIRECT = 0x800
 F_FP64_AUTO = 0x1000
 F_DENSE_SEGMENTS = 0x2000
+F_WARP_SEGMENTS = 0x4000  # segmented: whole segments per warp, no grid stage
 # status codes (sr_status)
 OK, ERR_ARG, ERR_DTYPE, ERR_LAUNCH, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 # barrier levels (sr_level)
@@ -168,6 +169,8 @@ def load():
                                      ctypes.POINTER(Config), vp]
     L.sr_reduce_sum_selected.restype = i32
     L.sr_reduce_sum_selected.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.sr_segmented_layout_flags.restype = i32
+    L.sr_segmented_layout_flags.argtypes = [i32, i32, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.sr_reduce_sum_segmented_selected.restype = i32
     L.sr_reduce_sum_segmented_selected.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.c_double, ctypes.c_double,
                                                    ctypes.c_double, vp]
@@ -503,6 +506,15 @@ def reduce_sum_segmented_selected_ptr(selector, x_ptr, offsets_ptr, nseg, dtype,
     return lib().sr_reduce_sum_segmented_selected(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(offsets_ptr),
                                                   int(nseg), int(dtype), ctypes.c_void_p(out_ptr), float(mean),
                                                   float(std), float(mx), ctypes.c_void_p(_stream(stream)))
+
+
+def segmented_layout_flags(sms, dtype, nseg, mean, std, mx) -> int:
+    """The form the selected segmented path applies for these statistics
+    (F_DENSE_SEGMENTS, F_WARP_SEGMENTS or 0); raises on bad arguments."""
+    r = lib().sr_segmented_layout_flags(int(sms), int(dtype), int(nseg), float(mean), float(std), float(mx))
+    if r < 0:
+        check(-r, "sr_segmented_layout_flags")
+    return r
 
 
 def plan(n: int, dtype: int, config: Config = None) -> Config:

@@ -601,4 +601,114 @@ inline const void* pick_seg_tma(int vec, int unroll) {
     return vec == 16 ? pick_seg_bulk<DT, COMP, 16>(unroll) : (vec == 32 ? pick_seg_bulk<DT, COMP, 32>(unroll) : nullptr);
 }
 
+// ------------------------------------------------ warp-per-segment form
+// SR_F_WARP_SEGMENTS: each warp sums whole segments, so no segment crosses a
+// warp and there is no grid stage (results are deterministic).  Warps take
+// blocks of G consecutive segments in turn (block b to warp b mod W, G =
+// ceil(nseg / W) clamped to 1..32); lane k holds offsets[bG + k], so a block
+// costs one coalesced offsets load.  Per segment, the elements before its
+// first VB-aligned address and after its last whole vector are single loads
+// by the first lanes; the vectors between are spread over the lanes, UNROLL
+// per lane and batch; then one warp reduction and one store.  Segments go in
+// pairs: both first batches are loaded before either is summed, so each warp
+// keeps two segments' loads in flight.
+template <int DT, bool COMP, int VB, int UNROLL>
+__global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
+    using A = typename Acc<DT, COMP>::T;
+    constexpr int EB = SegElem<DT>::v;
+    constexpr int PV = VB / EB;  // elements per lane vector
+    constexpr int W = VB / 4;    // 32-bit words per lane vector
+    grid_dependency_wait();
+    allow_dependents();
+    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t Wn = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t G = (p.nseg + Wn - 1) / Wn;
+    G = G < 1 ? 1 : (G > 32 ? 32 : G);
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(p.x);
+    for (int64_t b0 = w * G; b0 < p.nseg; b0 += Wn * G) {
+        const int64_t nb = (p.nseg - b0 < G) ? p.nseg - b0 : G;  // segments in this block
+        const int64_t i = b0 + (lane < nb ? lane : nb);           // lane nb (or 31) holds the end
+        const int64_t o = __ldg(p.offsets + i);
+        const int64_t o_end = __ldg(p.offsets + b0 + nb);
+        // two segments per step: both first batches of loads are in flight together
+        for (int k = 0; k < (int)nb; k += 2) {
+            const bool two = k + 1 < (int)nb;  // warp-uniform
+            int64_t s0[2], s1[2];
+            s0[0] = __shfl_sync(0xffffffffu, o, k);
+            s1[0] = two ? __shfl_sync(0xffffffffu, o, k + 1) : o_end;
+            s0[1] = s1[0];
+            s1[1] = !two ? s1[0] : ((k + 2 < (int)nb) ? __shfl_sync(0xffffffffu, o, k + 2) : o_end);
+            int64_t a0[2], nv[2];
+            A edge[2], acc[2][W];
+            uint32_t r[2][UNROLL][W];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                a0[j] = s0[j] + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0[j] * EB) % VB) % VB) / EB);
+                if (a0[j] > s1[j]) a0[j] = s1[j];
+                nv[j] = (s1[j] - a0[j]) / PV;
+                const int64_t a1 = a0[j] + nv[j] * PV;
+                edge[j] = Op<A>::zero();  // head [s0, a0) and tail [a1, s1), fewer than PV each
+                if (lane < a0[j] - s0[j]) acc_elem<DT>(edge[j], p.x, s0[j] + lane);
+                if (lane < s1[j] - a1) acc_elem<DT>(edge[j], p.x, a1 + lane);
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int64_t v = u * 32 + lane;
+                    if (v < nv[j]) ldg_vec(p.x + (a0[j] + v * PV) * EB, r[j][u]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int q = 0; q < W; ++q) acc[j][q] = Op<A>::zero();
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (u * 32 + lane < nv[j]) {
+#pragma unroll
+                        for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[j][u][q]);
+                    }
+                }
+                // the rest of a segment longer than one batch
+                const unsigned char* body = p.x + a0[j] * EB;
+                for (int64_t v0 = 32 * UNROLL; v0 < nv[j]; v0 += 32 * UNROLL) {
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        const int64_t v = v0 + u * 32 + lane;
+                        if (v < nv[j]) ldg_vec(body + v * VB, r[0][u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        if (v0 + u * 32 + lane < nv[j]) {
+#pragma unroll
+                            for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[0][u][q]);
+                        }
+                    }
+                }
+            }
+            const A t0 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[0]), edge[0]));
+            const A t1 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[1]), edge[1]));
+            if (lane == 0) {
+                seg_out(p, b0 + k, t0);
+                if (two) seg_out(p, b0 + k + 1, t1);
+            }
+        }
+    }
+}
+
+template <int DT, bool COMP, int VB>
+inline const void* pick_seg_warp_u(int unroll) {
+    switch (unroll) {
+    case 1: return (const void*)seg_warp_kernel<DT, COMP, VB, 1>;
+    case 2: return (const void*)seg_warp_kernel<DT, COMP, VB, 2>;
+    case 4: return (const void*)seg_warp_kernel<DT, COMP, VB, 4>;
+    case 8: return (const void*)seg_warp_kernel<DT, COMP, VB, 8>;
+    default: return nullptr;
+    }
+}
+template <int DT, bool COMP>
+inline const void* pick_seg_warp(int vec, int unroll) {
+    return vec == 16 ? pick_seg_warp_u<DT, COMP, 16>(unroll) : (vec == 32 ? pick_seg_warp_u<DT, COMP, 32>(unroll) : nullptr);
+}
+
 }  // namespace sr

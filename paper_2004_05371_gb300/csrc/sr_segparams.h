@@ -43,5 +43,10 @@ const void* seg_tma_bf16(bool comp, int vec, int unroll);
 const void* seg_ldg_fp8(bool comp, int vec, int unroll, const void** fin);
 const void* seg_dense_fp8(bool comp, int vec, int unroll);
 const void* seg_tma_fp8(bool comp, int vec, int unroll);
+// The warp-per-segment form, every dtype in one translation unit.
+const void* seg_warp_f32(bool comp, int vec, int unroll);
+const void* seg_warp_i32(bool comp, int vec, int unroll);
+const void* seg_warp_bf16(bool comp, int vec, int unroll);
+const void* seg_warp_fp8(bool comp, int vec, int unroll);
 
 }  // namespace sr

@@ -170,12 +170,43 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
     int st = s ? sr_selector_choose(s, n, dtype, nseg, len_mean, len_std, len_max, &c, stream)
                : tuned_config(x, n, offsets, nseg, dtype, out, len_mean, len_std, len_max, &c, stream);
     if (st != SR_OK) return st;
-    // Uniformly short segments (at most 512 bytes on average, spread at most half
-    // the mean: several segment ends per row of vectors, rarely two per lane)
-    // take the kernel with the warp-wide pass over such rows (SR_F_DENSE_SEGMENTS);
-    // measured 1.4-5.5x there, slower on mixed layouts, which this rule excludes.
-    if (len_mean * (double)elem_size(dtype) <= 512.0 && len_std <= 0.5 * len_mean) c.variant |= SR_F_DENSE_SEGMENTS;
+    const sr::DeviceInfo* d = sr::current_device(&st);
+    if (!d) return st;
+    const int form = sr_segmented_layout_flags(d->sms, dtype, nseg, len_mean, len_std, len_max);
+    if (form < 0) return -form;
+    if (form == SR_F_WARP_SEGMENTS) {  // the form's own launch shape; no grid stage, no ring
+        c.variant = (c.variant & ~(SR_F_BULK | SR_F_DENSE_SEGMENTS)) | SR_F_WARP_SEGMENTS;
+        c.vec_bytes = c.unroll = c.block_threads = c.stages = c.grid = c.ctas_per_sm = 0;
+    } else {
+        c.variant |= form;
+    }
     return sr_reduce_sum_segmented_ex(x, offsets, nseg, dtype, out, &c, stream);
+}
+
+// Uniformly short segments (spread at most half the mean: several segment
+// ends per row of vectors, rarely two per lane) take the kernel with the
+// warp-wide pass over such rows (SR_F_DENSE_SEGMENTS; measured 1.4-5.5x the
+// plain kernel there, slower on mixed layouts, which the rule excludes).
+// Very many segments (2^19 or more) none of which is far above one warp's
+// even share of the elements take the warp-per-segment form instead, except
+// the very shortest: measured at ~2^28 FP32 elements it is 1.6x the best
+// other form at 1M segments of 268 elements and at 4M lognormal ones of
+// median 40, 1.18x the dense kernel at 4M segments of 64, 2.9x slower than it
+// at 16M of 16 (the split, 128 bytes, lies between the last two); and
+// 15-50x slower at 10^4-10^5 lognormal segments, where a single warp holds a
+// long segment, which the rule excludes.  The share assumes 32 resident warps
+// per SM, the form's occupancy at its default shape.
+int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean, double len_std, double len_max) {
+    if (dtype < SR_F32 || dtype > SR_FP8E4M3) return -SR_ERR_DTYPE;
+    if (sms < 1 || nseg < 0 || !(len_mean >= 0.0) || !(len_std >= 0.0) || len_max != len_max) return -SR_ERR_ARG;
+    const double bytes = len_mean * (double)sr::elem_size(dtype);
+    const bool uniform = len_std <= 0.5 * len_mean;
+    if (bytes <= 128.0 && uniform) return SR_F_DENSE_SEGMENTS;
+    const double longest = len_max > 0.0 ? len_max : len_mean + 4.0 * len_std;
+    const double share = len_mean * (double)nseg / (32.0 * (double)sms);
+    if (nseg >= (int64_t)1 << 19 && longest <= 2.0 * share) return SR_F_WARP_SEGMENTS;
+    if (bytes <= 512.0 && uniform) return SR_F_DENSE_SEGMENTS;
+    return 0;
 }
 
 }  // extern "C"

@@ -96,6 +96,8 @@ def test_segmented_rejects_bad_arguments_without_gpu(lib):
     assert call(dtype=sr.I32, out=ALIGNED + 4) == sr.ERR_ARG       # int64 results need 8 bytes
     assert call(variant=sr.SINGLE_CLUSTER) == sr.ERR_UNSUPPORTED
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK | sr.F_DENSE_SEGMENTS) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.F_WARP_SEGMENTS | sr.F_BULK) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.ATOMIC | sr.F_WARP_SEGMENTS | sr.F_DENSE_SEGMENTS) == sr.ERR_UNSUPPORTED
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK, unroll=1) == sr.ERR_ARG     # TMA chunks: 2, 4 or 8 rows
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK, stages=9) == sr.ERR_ARG
     assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1)) == sr.ERR_UNSUPPORTED
@@ -227,3 +229,32 @@ def test_host_entry_rejects_without_gpu(lib):
     assert sr.reduce_sum_host_ptr(xp, 16, 8, op, None, stream=0) == sr.ERR_DTYPE
     assert sr.reduce_sum_host_ptr(xp, 16, sr.F32, op, sr.make_config(sr.ATOMIC), stream=0) == sr.ERR_UNSUPPORTED
     assert sr.reduce_sum_host_ptr(xp + 2, 4, sr.F32, op, None, stream=0) == sr.ERR_ARG
+
+
+def test_segmented_layout_flags_without_gpu(lib):
+    """The selected segmented path's form rule, a pure host function."""
+    f = sr.segmented_layout_flags
+    assert f(152, sr.F32, 20_000, 24.0, 0.0, 24.0) == sr.F_DENSE_SEGMENTS       # 96 bytes, uniform
+    assert f(152, sr.F32, 20_000, 128.0, 64.0, 0.0) == sr.F_DENSE_SEGMENTS      # 512 bytes, std = mean / 2
+    assert f(152, sr.F32, 20_000, 129.0, 0.0, 129.0) == 0                      # just over 512 bytes
+    assert f(152, sr.FP8E4M3, 20_000, 512.0, 0.0, 512.0) == sr.F_DENSE_SEGMENTS  # bytes, not elements
+    assert f(152, sr.F32, 1 << 20, 24.0, 20.0, 400.0) == sr.F_WARP_SEGMENTS    # spread: not dense
+    assert f(152, sr.F32, 1 << 22, 64.0, 0.0, 64.0) == sr.F_WARP_SEGMENTS      # 256 bytes: warp before dense
+    assert f(152, sr.F32, 1 << 22, 32.0, 0.0, 32.0) == sr.F_DENSE_SEGMENTS     # 128 bytes: dense first
+    assert f(152, sr.F32, 1 << 24, 16.0, 0.0, 16.0) == sr.F_DENSE_SEGMENTS
+    assert f(152, sr.F32, 1_000_000, 268.0, 0.0, 268.0) == sr.F_WARP_SEGMENTS
+    assert f(152, sr.F32, (1 << 19) - 1, 268.0, 0.0, 268.0) == 0               # too few segments
+    share = 268.0 * 1_000_000 / (32 * 152)
+    assert f(152, sr.F32, 1_000_000, 268.0, 50.0, 2 * share) == sr.F_WARP_SEGMENTS
+    assert f(152, sr.F32, 1_000_000, 268.0, 50.0, 2 * share + 1) == 0          # one segment too long
+    assert f(152, sr.F32, 1_000_000, 268.0, 20000.0, 0.0) == sr.F_WARP_SEGMENTS  # unknown max: mean + 4 std
+    assert f(152, sr.F32, 1_000_000, 268.0, 40000.0, 0.0) == 0
+    assert f(152, sr.F32, 10_000, 26843.5, 80000.0, 1 << 24) == 0               # the 10,000-segment batch
+    for bad in ((0, sr.F32, 10, 1.0, 0.0, 1.0), (152, sr.F32, -1, 1.0, 0.0, 1.0),
+                (152, sr.F32, 10, float("nan"), 0.0, 1.0), (152, sr.F32, 10, 1.0, -1.0, 1.0)):
+        with pytest.raises(sr.SRError) as e:
+            f(*bad)
+        assert e.value.status == sr.ERR_ARG
+    with pytest.raises(sr.SRError) as e:
+        f(152, 7, 10, 1.0, 0.0, 1.0)
+    assert e.value.status == sr.ERR_DTYPE
