@@ -111,8 +111,8 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
         if (!c.block_threads) p.block = 512;
     }
     // Without an explicit shape, many segments (kSegBulkMin or more) take the TMA
-    // form: measured 1.13-1.93x the LDG default from 100,000 to 16M segments of
-    // ~2^28 elements, 2 % behind it at 10,000.
+    // form: measured 1.02-1.41x the LDG default from 100,000 to 16M segments of
+    // ~2^28 elements, 1 % behind it at 10,000.
     const bool shape_given = c.vec_bytes || c.unroll || c.block_threads || c.stages;
     p.bulk = (c.variant & SR_F_BULK) != 0 || (!shape_given && !p.dense && !p.warp && nseg >= kSegBulkMin);
     if (p.bulk) {  // per-warp ring: stages x (unroll rows of 32 vectors) + one mbarrier per stage
