@@ -113,6 +113,13 @@ typedef enum {
                                    (default 16 bytes x 2; unroll 1/2/4/8).  Not with
                                    SR_F_BULK or SR_F_DENSE_SEGMENTS
                                    (SR_ERR_UNSUPPORTED). */
+#define SR_F_LANE_SEGMENTS 0x8000 /* segmented only: each thread sums whole segments
+                                   alone (thread t takes segments t, t + T, ...), so a
+                                   warp covers 32 consecutive segments with coalesced
+                                   offsets and results; `unroll` (1/2/4/8, default 4)
+                                   independent element loads per step.  For very short
+                                   segments.  No grid stage; deterministic.  Not with
+                                   another form flag (SR_ERR_UNSUPPORTED). */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses
@@ -263,13 +270,14 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * expired one reported as SR_ERR_TIMEOUT by sr_stream_status).  Without an
  * explicit shape (vec_bytes, unroll, block_threads and stages all 0) calls
  * with 32768 or more segments take the TMA form, fewer the LDG one.
- * With SR_F_WARP_SEGMENTS whole segments go to single warps instead (see the
- * flag).
+ * With SR_F_WARP_SEGMENTS whole segments go to single warps instead, with
+ * SR_F_LANE_SEGMENTS to single threads (see the flags).
  * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE, SR_F_BULK,
- * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS), block_threads (at most 512), ctas_per_sm, grid (at
+ * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS, SR_F_LANE_SEGMENTS), block_threads (at most 512), ctas_per_sm, grid (at
  * most 65536 warps in total), vec_bytes, unroll, stages (TMA form), scale
  * (FP8).  SR_SINGLE_CLUSTER, cluster bits, and any two of SR_F_BULK,
- * SR_F_DENSE_SEGMENTS and SR_F_WARP_SEGMENTS -> SR_ERR_UNSUPPORTED; a ring larger than a CTA's
+ * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS and SR_F_LANE_SEGMENTS ->
+ * SR_ERR_UNSUPPORTED; a ring larger than a CTA's
  * shared memory -> SR_ERR_LAUNCH.
  * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,
  * bad config), SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
@@ -469,12 +477,15 @@ int sr_selector_choose(sr_selector selector, int64_t n, int dtype, int64_t nseg,
  * takes the segment-length statistics from the caller (n = mean * nseg) and
  * applies the form sr_segmented_layout_flags gives for them: it adds
  * SR_F_DENSE_SEGMENTS to the chosen configuration, or replaces the chosen
- * configuration's shape with SR_F_WARP_SEGMENTS at its default shape. */
+ * configuration's shape with SR_F_WARP_SEGMENTS or SR_F_LANE_SEGMENTS at its
+ * default shape. */
 int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int dtype, void* out,
                            sr_stream_t stream);
 /* The segmented form for a layout, from the caller's segment-length
  * statistics (mean, standard deviation, maximum; len_max <= 0 when unknown,
  * then mean + 4 std stands in) and the device's SM count, in this order:
+ * SR_F_LANE_SEGMENTS for 2^19 or more uniform segments (std <= mean / 2) of
+ * at most 64 bytes on average and none above 4x the mean;
  * SR_F_DENSE_SEGMENTS for uniformly very short segments (mean * element size
  * <= 128 bytes, std <= mean / 2); SR_F_WARP_SEGMENTS for 2^19 or more
  * segments none longer than twice a warp's even share of the elements

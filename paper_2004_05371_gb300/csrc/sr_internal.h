@@ -64,7 +64,7 @@ struct SegPlan {
     int dtype = 0;
     int64_t nseg = 0;
     int stage = 0;
-    bool comp = false, fp64 = false, dense = false, bulk = false, warp = false;
+    bool comp = false, fp64 = false, dense = false, bulk = false, warp = false, lane = false;
     int vec = 16, unroll = 4, block = 256, grid = 0;
     int stages = 0;
     size_t smem = 0;  // dynamic shared memory of the TMA form

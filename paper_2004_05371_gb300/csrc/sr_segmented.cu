@@ -28,25 +28,33 @@ __global__ void __launch_bounds__(256) seg_check_kernel(const int64_t* offsets, 
     }
 }
 constexpr int kKnownSegFlags =
-    SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_DENSE_SEGMENTS | SR_F_BULK | SR_F_WARP_SEGMENTS;
+    SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_DENSE_SEGMENTS | SR_F_BULK | SR_F_WARP_SEGMENTS |
+    SR_F_LANE_SEGMENTS;
+// the load-path / form flags, at most one of which a segmented call may set
+constexpr int kSegFormFlags = SR_F_DENSE_SEGMENTS | SR_F_BULK | SR_F_WARP_SEGMENTS | SR_F_LANE_SEGMENTS;
 constexpr int64_t kSegBulkMin = 32768;  // segments from which the default shape is the TMA form
 
-bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, bool bulk, bool warp, const void** main,
-                 const void** fin) {
+bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, bool bulk, bool warp, bool lane,
+                 const void** main, const void** fin) {
     const void* (*ldg)(bool, int, int, const void**) = nullptr;
     const void* (*den)(bool, int, int) = nullptr;
     const void* (*tma)(bool, int, int) = nullptr;
     const void* (*wrp)(bool, int, int) = nullptr;
+    const void* (*lan)(bool, int) = nullptr;
     switch (dtype) {
-    case SR_F32: ldg = seg_ldg_f32; den = seg_dense_f32; tma = seg_tma_f32; wrp = seg_warp_f32; break;
-    case SR_I32: ldg = seg_ldg_i32; den = seg_dense_i32; tma = seg_tma_i32; wrp = seg_warp_i32; break;
-    case SR_BF16: ldg = seg_ldg_bf16; den = seg_dense_bf16; tma = seg_tma_bf16; wrp = seg_warp_bf16; break;
-    case SR_FP8E4M3: ldg = seg_ldg_fp8; den = seg_dense_fp8; tma = seg_tma_fp8; wrp = seg_warp_fp8; break;
+    case SR_F32: ldg = seg_ldg_f32; den = seg_dense_f32; tma = seg_tma_f32; wrp = seg_warp_f32; lan = seg_lane_f32; break;
+    case SR_I32: ldg = seg_ldg_i32; den = seg_dense_i32; tma = seg_tma_i32; wrp = seg_warp_i32; lan = seg_lane_i32; break;
+    case SR_BF16:
+        ldg = seg_ldg_bf16; den = seg_dense_bf16; tma = seg_tma_bf16; wrp = seg_warp_bf16; lan = seg_lane_bf16;
+        break;
+    case SR_FP8E4M3:
+        ldg = seg_ldg_fp8; den = seg_dense_fp8; tma = seg_tma_fp8; wrp = seg_warp_fp8; lan = seg_lane_fp8;
+        break;
     default: return false;
     }
-    if (warp) {  // one kernel, nothing to finish
+    if (warp || lane) {  // one kernel, nothing to finish
         *fin = nullptr;
-        *main = (dense || bulk) ? nullptr : wrp(comp, vec, unroll);
+        *main = (dense || bulk || (warp && lane)) ? nullptr : (warp ? wrp(comp, vec, unroll) : lan(comp, unroll));
         return *main != nullptr;
     }
     const void* plain = ldg(comp, vec, unroll, fin);  // also sets the second kernel
@@ -67,8 +75,8 @@ int seg_validate(const void* x, const int64_t* offsets, int64_t nseg, int dtype,
     if (out && reinterpret_cast<uintptr_t>(out) % ((dtype == SR_I32 || fp64) ? 8 : 4)) return SR_ERR_ARG;
     if (c.variant & ~kKnownSegFlags)
         return (c.variant & (SR_CLUSTER_MASK | SR_F_FP64_AUTO)) ? SR_ERR_UNSUPPORTED : SR_ERR_ARG;
-    if ((c.variant & SR_F_BULK) && (c.variant & SR_F_DENSE_SEGMENTS)) return SR_ERR_UNSUPPORTED;
-    if ((c.variant & SR_F_WARP_SEGMENTS) && (c.variant & (SR_F_BULK | SR_F_DENSE_SEGMENTS))) return SR_ERR_UNSUPPORTED;
+    const int forms = c.variant & kSegFormFlags;
+    if (forms & (forms - 1)) return SR_ERR_UNSUPPORTED;  // two forms at once
     if ((c.variant & SR_F_BULK) && (c.unroll == 1)) return SR_ERR_ARG;  // chunks of 2, 4 or 8 rows
     if (c.stages != 0 && (c.stages < 2 || c.stages > 8)) return SR_ERR_ARG;
     const int stage = c.variant & SR_STAGE_MASK;
@@ -102,6 +110,11 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     p.scale = (dtype == SR_FP8E4M3 && c.scale != 0.f) ? c.scale : 1.f;
     p.dense = (c.variant & SR_F_DENSE_SEGMENTS) != 0;
     p.warp = (c.variant & SR_F_WARP_SEGMENTS) != 0;
+    p.lane = (c.variant & SR_F_LANE_SEGMENTS) != 0;
+    if (p.lane) {  // element loads: vec_bytes plays no part
+        p.vec = c.vec_bytes ? c.vec_bytes : 16;
+        p.unroll = c.unroll ? c.unroll : 4;
+    }
     if (p.warp) {  // 16-byte vectors, 2 per lane and segment (64 registers: 32 warps per SM)
         p.vec = c.vec_bytes ? c.vec_bytes : 16;
         p.unroll = c.unroll ? c.unroll : 2;
@@ -114,14 +127,14 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     // form: measured 1.02-1.41x the LDG default from 100,000 to 16M segments of
     // ~2^28 elements, 1 % behind it at 10,000.
     const bool shape_given = c.vec_bytes || c.unroll || c.block_threads || c.stages;
-    p.bulk = (c.variant & SR_F_BULK) != 0 || (!shape_given && !p.dense && !p.warp && nseg >= kSegBulkMin);
+    p.bulk = (c.variant & SR_F_BULK) != 0 || (!shape_given && !p.dense && !p.warp && !p.lane && nseg >= kSegBulkMin);
     if (p.bulk) {  // per-warp ring: stages x (unroll rows of 32 vectors) + one mbarrier per stage
         if (!c.unroll) p.unroll = 4;
         p.stages = c.stages ? c.stages : 2;
         p.smem = (size_t)(p.block / 32) * p.stages * ((size_t)p.unroll * 32 * p.vec + 8);
         if (p.smem > (size_t)d.smem_per_block_optin) return SR_ERR_LAUNCH;
     }
-    if (!seg_kernels(dtype, p.comp, p.vec, p.unroll, p.dense, p.bulk, p.warp, &p.main, &p.fin))
+    if (!seg_kernels(dtype, p.comp, p.vec, p.unroll, p.dense, p.bulk, p.warp, p.lane, &p.main, &p.fin))
         return SR_ERR_UNSUPPORTED;
     int st = prepare_function(p.main, p.smem, false);
     if (st != SR_OK) return st;
@@ -132,7 +145,7 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     int per_sm = c.ctas_per_sm ? std::min(c.ctas_per_sm, resident) : resident;
     int64_t grid = c.grid ? c.grid : (int64_t)d.sms * per_sm;
     grid = std::min<int64_t>(grid, kSegMaxWarps / (p.block / 32));
-    if (p.stage == SR_GRID_SYNC && !p.warp && grid > (int64_t)resident * d.sms) {
+    if (p.stage == SR_GRID_SYNC && !p.warp && !p.lane && grid > (int64_t)resident * d.sms) {
         if (c.grid) return SR_ERR_LAUNCH;  // cannot be co-resident: never launched
         grid = (int64_t)resident * d.sms;
     }
@@ -182,7 +195,7 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
     kp.stage = p.stage;
     kp.fp64 = p.fp64 ? 1 : 0;
     cudaError_t e;
-    if (p.stage == SR_ATOMIC && !p.warp) {
+    if (p.stage == SR_ATOMIC && !p.warp && !p.lane) {
         const size_t ob = (p.dtype == SR_I32 || p.fp64) ? 8 : 4;
         const int zs = launch_zero(out, ob * (size_t)p.nseg, s);
         if (zs != SR_OK) return zs;
@@ -199,7 +212,7 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
     lc.stream = s;
     lc.attrs = pdl;
     lc.numAttrs = 1;
-    if (p.stage == SR_GRID_SYNC && !p.warp) {
+    if (p.stage == SR_GRID_SYNC && !p.warp && !p.lane) {
         e = cudaLaunchCooperativeKernel(p.main, dim3(p.grid), dim3(p.block), args, p.smem, s);
     } else {
         lc.gridDim = dim3(p.grid);
@@ -209,7 +222,7 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
         lc.dynamicSmemBytes = 0;
     }
     if (e != cudaSuccess) return status_from_cuda(e);
-    if (p.stage == SR_TWO_KERNEL && !p.warp) {
+    if (p.stage == SR_TWO_KERNEL && !p.warp && !p.lane) {
         int64_t wn = p.warps;
         int pv = p.vec / elem_size(p.dtype);
         void* fargs[] = {&kp, &wn, &pv};

@@ -696,6 +696,50 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
     }
 }
 
+// ------------------------------------------------ lane-per-segment form
+// SR_F_LANE_SEGMENTS: thread t of the grid sums segments t, t + T, ... alone
+// (T threads), so a warp covers 32 consecutive segments: the offsets and the
+// results move as coalesced words, and the lanes' element loads fall into the
+// warp's contiguous range (one line serves neighbouring lanes).  UNROLL
+// independent element loads per step feed UNROLL accumulators, summed as a
+// pairwise tree.  For very short segments only: a lane walks its segment
+// alone.  No grid stage; deterministic.
+template <int DT, bool COMP, int UNROLL>
+__global__ void __launch_bounds__(512) seg_lane_kernel(const SegParams p) {
+    using A = typename Acc<DT, COMP>::T;
+    grid_dependency_wait();
+    allow_dependents();
+    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += T) {
+        const int64_t s0 = __ldg(p.offsets + s);
+        const int64_t s1 = __ldg(p.offsets + s + 1);
+        A acc[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) acc[u] = Op<A>::zero();
+        int64_t i = s0;
+        for (; i + UNROLL <= s1; i += UNROLL) {
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) acc_elem<DT>(acc[u], p.x, i + u);
+        }
+#pragma unroll
+        for (int u = 0; u + 1 < UNROLL; ++u)
+            if (i + u < s1) acc_elem<DT>(acc[u], p.x, i + u);
+        seg_out(p, s, sum_words<A, UNROLL>(acc));
+    }
+}
+
+template <int DT, bool COMP>
+inline const void* pick_seg_lane(int unroll) {
+    switch (unroll) {
+    case 1: return (const void*)seg_lane_kernel<DT, COMP, 1>;
+    case 2: return (const void*)seg_lane_kernel<DT, COMP, 2>;
+    case 4: return (const void*)seg_lane_kernel<DT, COMP, 4>;
+    case 8: return (const void*)seg_lane_kernel<DT, COMP, 8>;
+    default: return nullptr;
+    }
+}
+
 template <int DT, bool COMP, int VB>
 inline const void* pick_seg_warp_u(int unroll) {
     switch (unroll) {

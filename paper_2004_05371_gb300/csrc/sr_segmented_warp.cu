@@ -1,4 +1,5 @@
-// Segmented-sum kernels of every input dtype: the warp-per-segment form (SR_F_WARP_SEGMENTS).
+// Segmented-sum kernels of every input dtype: the warp-per-segment form
+// (SR_F_WARP_SEGMENTS) and the lane-per-segment form (SR_F_LANE_SEGMENTS).
 #include "sr_segmented_kernels.cuh"
 
 namespace sr {
@@ -14,5 +15,18 @@ const void* seg_warp_bf16(bool comp, int vec, int unroll) {
 }
 const void* seg_warp_fp8(bool comp, int vec, int unroll) {
     return comp ? pick_seg_warp<kDtFP8, true>(vec, unroll) : pick_seg_warp<kDtFP8, false>(vec, unroll);
+}
+const void* seg_lane_f32(bool comp, int unroll) {
+    return comp ? pick_seg_lane<kDtF32, true>(unroll) : pick_seg_lane<kDtF32, false>(unroll);
+}
+const void* seg_lane_i32(bool comp, int unroll) {
+    (void)comp;  // integer sums are exact
+    return pick_seg_lane<kDtI32, false>(unroll);
+}
+const void* seg_lane_bf16(bool comp, int unroll) {
+    return comp ? pick_seg_lane<kDtBF16, true>(unroll) : pick_seg_lane<kDtBF16, false>(unroll);
+}
+const void* seg_lane_fp8(bool comp, int unroll) {
+    return comp ? pick_seg_lane<kDtFP8, true>(unroll) : pick_seg_lane<kDtFP8, false>(unroll);
 }
 }  // namespace sr

@@ -174,8 +174,8 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
     if (!d) return st;
     const int form = sr_segmented_layout_flags(d->sms, dtype, nseg, len_mean, len_std, len_max);
     if (form < 0) return -form;
-    if (form == SR_F_WARP_SEGMENTS) {  // the form's own launch shape; no grid stage, no ring
-        c.variant = (c.variant & ~(SR_F_BULK | SR_F_DENSE_SEGMENTS)) | SR_F_WARP_SEGMENTS;
+    if (form == SR_F_WARP_SEGMENTS || form == SR_F_LANE_SEGMENTS) {  // the form's own shape; no grid stage
+        c.variant = (c.variant & ~(SR_F_BULK | SR_F_DENSE_SEGMENTS)) | form;
         c.vec_bytes = c.unroll = c.block_threads = c.stages = c.grid = c.ctas_per_sm = 0;
     } else {
         c.variant |= form;
@@ -183,28 +183,34 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
     return sr_reduce_sum_segmented_ex(x, offsets, nseg, dtype, out, &c, stream);
 }
 
-// Uniformly short segments (spread at most half the mean: several segment
-// ends per row of vectors, rarely two per lane) take the kernel with the
-// warp-wide pass over such rows (SR_F_DENSE_SEGMENTS; measured 1.4-5.5x the
-// plain kernel there, slower on mixed layouts, which the rule excludes).
-// Very many segments (2^19 or more) none of which is far above one warp's
-// even share of the elements take the warp-per-segment form instead, except
-// the very shortest: measured at ~2^28 FP32 elements it is 1.6x the best
-// other form at 1M segments of 268 elements and at 4M lognormal ones of
-// median 40, 1.18x the dense kernel at 4M segments of 64, 2.9x slower than it
-// at 16M of 16 (the split, 128 bytes, lies between the last two); and
-// 15-50x slower at 10^4-10^5 lognormal segments, where a single warp holds a
-// long segment, which the rule excludes.  The share assumes 32 resident warps
-// per SM, the form's occupancy at its default shape.
+// Measured at ~2^28 FP32 elements (U[-1,1]) against every form:
+//  - 16M segments of 16 elements: one thread per segment (SR_F_LANE_SEGMENTS)
+//    453 us, the dense kernel 711, one warp per segment 2050;
+//  - 4M of 64: one warp per segment (pairs, 16 B x 2) 515 us, dense 610;
+//  - 1M of 268: warp 204 us, 1.6x the best flat-split form; 4M lognormal of
+//    median 40 (empty ones included): warp 602 us, 1.6x;
+//  - 10^4-10^5 lognormal segments: the flat split (LDG below 32,768
+//    segments, the TMA ring above); the whole-segment forms are 15-800x
+//    slower there, one warp or thread holding a segment of millions.
+// The dense kernel (a warp-wide pass over rows with many segment ends) is
+// 1.4-5.5x the plain kernel on uniformly short segments of fewer segments.
+// The rule keeps each form inside the range it was measured in: the thread
+// form for uniform segments of at most 64 bytes with none above 4x the mean;
+// the dense kernel up to 128 bytes (uniform); the warp form for 2^19 or more
+// segments none of which exceeds twice a warp's even share of the elements
+// (32 resident warps per SM, its occupancy at its default shape); the dense
+// kernel up to 512 bytes (uniform); else the plain form.
 int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean, double len_std, double len_max) {
     if (dtype < SR_F32 || dtype > SR_FP8E4M3) return -SR_ERR_DTYPE;
     if (sms < 1 || nseg < 0 || !(len_mean >= 0.0) || !(len_std >= 0.0) || len_max != len_max) return -SR_ERR_ARG;
     const double bytes = len_mean * (double)sr::elem_size(dtype);
     const bool uniform = len_std <= 0.5 * len_mean;
-    if (bytes <= 128.0 && uniform) return SR_F_DENSE_SEGMENTS;
+    const bool many = nseg >= (int64_t)1 << 19;
     const double longest = len_max > 0.0 ? len_max : len_mean + 4.0 * len_std;
+    if (many && bytes <= 64.0 && uniform && longest <= 4.0 * len_mean) return SR_F_LANE_SEGMENTS;
+    if (bytes <= 128.0 && uniform) return SR_F_DENSE_SEGMENTS;
     const double share = len_mean * (double)nseg / (32.0 * (double)sms);
-    if (nseg >= (int64_t)1 << 19 && longest <= 2.0 * share) return SR_F_WARP_SEGMENTS;
+    if (many && longest <= 2.0 * share) return SR_F_WARP_SEGMENTS;
     if (bytes <= 512.0 && uniform) return SR_F_DENSE_SEGMENTS;
     return 0;
 }

@@ -98,6 +98,8 @@ def test_segmented_rejects_bad_arguments_without_gpu(lib):
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK | sr.F_DENSE_SEGMENTS) == sr.ERR_UNSUPPORTED
     assert call(variant=sr.LAST_BLOCK | sr.F_WARP_SEGMENTS | sr.F_BULK) == sr.ERR_UNSUPPORTED
     assert call(variant=sr.ATOMIC | sr.F_WARP_SEGMENTS | sr.F_DENSE_SEGMENTS) == sr.ERR_UNSUPPORTED
+    for other in (sr.F_BULK, sr.F_DENSE_SEGMENTS, sr.F_WARP_SEGMENTS):
+        assert call(variant=sr.TWO_KERNEL | sr.F_LANE_SEGMENTS | other) == sr.ERR_UNSUPPORTED
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK, unroll=1) == sr.ERR_ARG     # TMA chunks: 2, 4 or 8 rows
     assert call(variant=sr.LAST_BLOCK | sr.F_BULK, stages=9) == sr.ERR_ARG
     assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1)) == sr.ERR_UNSUPPORTED
@@ -241,7 +243,10 @@ def test_segmented_layout_flags_without_gpu(lib):
     assert f(152, sr.F32, 1 << 20, 24.0, 20.0, 400.0) == sr.F_WARP_SEGMENTS    # spread: not dense
     assert f(152, sr.F32, 1 << 22, 64.0, 0.0, 64.0) == sr.F_WARP_SEGMENTS      # 256 bytes: warp before dense
     assert f(152, sr.F32, 1 << 22, 32.0, 0.0, 32.0) == sr.F_DENSE_SEGMENTS     # 128 bytes: dense first
-    assert f(152, sr.F32, 1 << 24, 16.0, 0.0, 16.0) == sr.F_DENSE_SEGMENTS
+    assert f(152, sr.F32, 1 << 24, 16.0, 0.0, 16.0) == sr.F_LANE_SEGMENTS      # 64 bytes, many: a thread each
+    assert f(152, sr.F32, 1 << 24, 16.0, 4.0, 65.0) == sr.F_DENSE_SEGMENTS     # one segment above 4x the mean
+    assert f(152, sr.F32, 1 << 18, 16.0, 0.0, 16.0) == sr.F_DENSE_SEGMENTS     # too few for the thread form
+    assert f(152, sr.F32, 1 << 24, 17.0, 0.0, 17.0) == sr.F_DENSE_SEGMENTS     # 68 bytes
     assert f(152, sr.F32, 1_000_000, 268.0, 0.0, 268.0) == sr.F_WARP_SEGMENTS
     assert f(152, sr.F32, (1 << 19) - 1, 268.0, 0.0, 268.0) == 0               # too few segments
     share = 268.0 * 1_000_000 / (32 * 152)

@@ -177,4 +177,17 @@ def test_selected_entry_points(sr):
         sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), nseg, sr.I32, out.data_ptr(),
                                                       lens.mean(), lens.std(), lens.max()))
         assert np.array_equal(out.cpu().numpy(), ref)
+    # very many tiny segments: the selected call takes SR_F_LANE_SEGMENTS
+    lens = np.random.default_rng(7).integers(8, 17, nseg).astype(np.int64)
+    off = np.zeros(nseg + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    assert sr.segmented_layout_flags(sms, sr.I32, nseg, lens.mean(), lens.std(), lens.max()) == sr.F_LANE_SEGMENTS
+    x = workloads.uniform_i32(int(off[-1]), seed=7)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
+    ref = oracle.segsum_i32(x, off)
+    for s in (nat, None):
+        out.fill_(-1)
+        sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), nseg, sr.I32, out.data_ptr(),
+                                                      lens.mean(), lens.std(), lens.max()))
+        assert np.array_equal(out.cpu().numpy(), ref)
     nat.close()

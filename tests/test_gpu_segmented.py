@@ -317,14 +317,19 @@ def test_default_load_path_by_segment_count(sr):
 WARP = 0x4000  # SR_F_WARPSEGMENTS: whole segments per warp, no grid stage
 
 
-@pytest.mark.parametrize("vec,unroll,block", [(16, 4, 256), (32, 1, 64), (16, 8, 512), (32, 2, 128), (16, 1, 32),
-                                              (32, 8, 256)])
-def test_warp_segments(sr, vec, unroll, block):
-    """The warp-per-segment form: random layouts with empty, tiny and long
-    segments (one of 100,000 elements summed by a single warp), aligned and
-    misaligned data, grids from one CTA (32 segments per warp block) to the
-    default; the stage bits change nothing.  Bit-exact for int32, within the
-    gates for binary32 (plain, compensated, binary64 output)."""
+LANE = 0x8000  # SR_F_LANE_SEGMENTS: whole segments per thread, no grid stage
+
+
+@pytest.mark.parametrize("form,vec,unroll,block", [
+    (WARP, 16, 4, 256), (WARP, 32, 1, 64), (WARP, 16, 8, 512), (WARP, 32, 2, 128), (WARP, 16, 1, 32),
+    (WARP, 32, 8, 256), (LANE, 16, 4, 256), (LANE, 16, 1, 32), (LANE, 32, 8, 512), (LANE, 16, 2, 128)])
+def test_warp_segments(sr, form, vec, unroll, block):
+    """The whole-segment forms (a warp, or a single thread, per segment):
+    random layouts with empty, tiny and long segments (one of 100,000
+    elements summed by a single warp or thread), aligned and misaligned data,
+    grids from one CTA (32 segments per warp block) to the default; the stage
+    bits change nothing.  Bit-exact for int32, within the gates for binary32
+    (plain, compensated, binary64 output)."""
     for nseg, max_len in ((1, 100_000), (2, 5), (33, 7), (500, 300), (5000, 40), (300, 20_000)):
         off = workloads.random_segment_offsets(nseg, max_len, seed=nseg + max_len + vec)
         n = int(off[-1])
@@ -333,22 +338,24 @@ def test_warp_segments(sr, vec, unroll, block):
         shape = dict(vec_bytes=vec, unroll=unroll, block_threads=block)
         for grid in (0, 1, 3):
             for x_off in (0, 1, 3):
-                _check(sr, xi, off, WARP | STAGES[(grid + x_off) % 4], x_off, grid=grid, **shape)
-                _check(sr, xf, off, WARP | STAGES[(grid + x_off + 1) % 4], x_off, grid=grid, **shape)
-        _check(sr, xf, off, WARP | sr.LAST_BLOCK | 0x100, **shape)
-        _check(sr, xf, off, WARP | sr.ATOMIC | 0x300, **shape)
+                _check(sr, xi, off, form | STAGES[(grid + x_off) % 4], x_off, grid=grid, **shape)
+                _check(sr, xf, off, form | STAGES[(grid + x_off + 1) % 4], x_off, grid=grid, **shape)
+        _check(sr, xf, off, form | sr.LAST_BLOCK | 0x100, **shape)
+        _check(sr, xf, off, form | sr.ATOMIC | 0x300, **shape)
 
 
+@pytest.mark.parametrize("form", [0x4000, 0x8000])
 @pytest.mark.parametrize("seg_len", [1, 3, 16, 64, 255, 268, 1000, 4097])
-def test_warp_segments_equal_lengths(sr, seg_len):
+def test_warp_segments_equal_lengths(sr, seg_len, form):
     """Equal segments of every alignment against the 16/32-byte vectors (the
-    head and tail elements take single loads); default shape, every dtype."""
+    head and tail elements take single loads) for the warp form, and against
+    the element steps of the lane form; default shapes, every dtype."""
     nseg = max(1, (1 << 20) // seg_len)
     off = np.arange(nseg + 1, dtype=np.int64) * seg_len
     n = int(off[-1])
     for x_off in (0, 1, 2):
-        _check(sr, workloads.uniform_i32(n, seed=seg_len), off, WARP, x_off)
-        _check(sr, workloads.uniform_f32(n, seed=seg_len), off, WARP | sr.ATOMIC, x_off)
+        _check(sr, workloads.uniform_i32(n, seed=seg_len), off, form, x_off)
+        _check(sr, workloads.uniform_f32(n, seed=seg_len), off, form | sr.ATOMIC, x_off)
     x = workloads.lognormal_f32(n, seed=seg_len, sigma=2.0)
     bits = workloads.to_bf16_bits(x)
     dec_b = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
@@ -356,11 +363,11 @@ def test_warp_segments_equal_lengths(sr, seg_len):
     od = torch.from_numpy(off).cuda()
     for x_off in (0, 1, 5):
         xd_b = _dev(bits.view(np.int16), x_off).view(torch.bfloat16)
-        got = sr.reduce_sum_segmented(xd_b, od, variant=WARP).cpu().numpy()
+        got = sr.reduce_sum_segmented(xd_b, od, variant=form).cpu().numpy()
         assert np.all(np.abs(got - oracle.segexact_f32(dec_b, off)) <=
                       4 * EPS32 * oracle.segsum_abs_f32(dec_b, off) + 1e-30), x_off
         xd_f = _dev(codes, x_off)
-        got = sr.reduce_sum_segmented(xd_f, od, config=sr.make_config(WARP, scale=deq)).cpu().numpy()
+        got = sr.reduce_sum_segmented(xd_f, od, config=sr.make_config(form, scale=deq)).cpu().numpy()
         for s in range(0, nseg, max(1, nseg // 50)):
             a, b = off[s], off[s + 1]
             exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
@@ -372,18 +379,21 @@ def test_warp_segments_plan_and_determinism(sr):
     assert r.variant & WARP and not r.variant & BULK and (r.vec_bytes, r.unroll) == (16, 2)
     r = sr.plan_segmented(1 << 20, sr.F32, sr.make_config(WARP))   # many segments: still no TMA form
     assert r.variant & WARP and not r.variant & BULK
-    for other in (BULK, DENSE):
+    for other in (BULK, DENSE, LANE):
         with pytest.raises(sr.SRError) as e:
             sr.plan_segmented(1000, sr.F32, sr.make_config(sr.LAST_BLOCK | WARP | other))
         assert e.value.status == sr.ERR_UNSUPPORTED
+    r = sr.plan_segmented(1 << 20, sr.F32, sr.make_config(LANE))
+    assert r.variant & LANE and not r.variant & BULK and r.unroll == 4
     off = workloads.segment_offsets(3000, 1 << 22, seed=18, median=512, sigma=1.0, hi=1 << 16)
     xd, od = _dev(workloads.uniform_f32(int(off[-1]), seed=18)), torch.from_numpy(off).cuda()
-    outs = [sr.reduce_sum_segmented(xd, od, variant=WARP | st).cpu().numpy() for st in STAGES]
-    assert all(np.array_equal(outs[0], o) for o in outs[1:])   # same kernel, same order, any stage bits
+    for form in (WARP, LANE):
+        outs = [sr.reduce_sum_segmented(xd, od, variant=form | st).cpu().numpy() for st in STAGES]
+        assert all(np.array_equal(outs[0], o) for o in outs[1:])   # same kernel, same order, any stage bits
 
 
 @pytest.mark.parametrize("stage", STAGES)
-@pytest.mark.parametrize("flags", [0, BULK, WARP])
+@pytest.mark.parametrize("flags", [0, BULK, WARP, LANE])
 def test_checked_entry(sr, stage, flags):
     """sr_reduce_sum_segmented_checked: valid offsets give the oracle's sums;
     offsets past the declared element count, a decreasing pair or a negative
@@ -420,6 +430,6 @@ def test_checked_entry(sr, stage, flags):
     for bad in (past, swapped, negative):
         st, got = run(bad)
         assert st == sr.ERR_ARG
-        assert np.all(got == (0 if stage == sr.ATOMIC and not flags & WARP else -7))   # nothing summed
+        assert np.all(got == (0 if stage == sr.ATOMIC and not flags & (WARP | LANE) else -7))   # nothing summed
     st, got = run(good)
     assert st == sr.OK and np.array_equal(got, oracle.segsum_i32(x, good))
