@@ -116,10 +116,11 @@ typedef enum {
 #define SR_F_LANE_SEGMENTS 0x8000 /* segmented only: each thread sums whole segments
                                    alone (thread t takes segments t, t + T, ...), so a
                                    warp covers 32 consecutive segments with coalesced
-                                   offsets and results; `unroll` (1/2/4/8, default 4)
-                                   independent element loads per step.  For very short
-                                   segments.  No grid stage; deterministic.  Not with
-                                   another form flag (SR_ERR_UNSUPPORTED). */
+                                   offsets and results; 16-byte vector loads of each
+                                   segment's aligned body, `unroll` (1/2/4/8, default 4)
+                                   per step.  For very short segments.  No grid stage;
+                                   deterministic.  Not with another form flag
+                                   (SR_ERR_UNSUPPORTED). */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses
@@ -485,7 +486,7 @@ int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int d
  * statistics (mean, standard deviation, maximum; len_max <= 0 when unknown,
  * then mean + 4 std stands in) and the device's SM count, in this order:
  * SR_F_LANE_SEGMENTS for 2^19 or more uniform segments (std <= mean / 2) of
- * at most 64 bytes on average and none above 4x the mean;
+ * at most 512 bytes on average and none above 4x the mean;
  * SR_F_DENSE_SEGMENTS for uniformly very short segments (mean * element size
  * <= 128 bytes, std <= mean / 2); SR_F_WARP_SEGMENTS for 2^19 or more
  * segments none longer than twice a warp's even share of the elements

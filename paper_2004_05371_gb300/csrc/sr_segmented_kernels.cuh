@@ -699,33 +699,58 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
 // ------------------------------------------------ lane-per-segment form
 // SR_F_LANE_SEGMENTS: thread t of the grid sums segments t, t + T, ... alone
 // (T threads), so a warp covers 32 consecutive segments: the offsets and the
-// results move as coalesced words, and the lanes' element loads fall into the
-// warp's contiguous range (one line serves neighbouring lanes).  UNROLL
-// independent element loads per step feed UNROLL accumulators, summed as a
-// pairwise tree.  For very short segments only: a lane walks its segment
-// alone.  No grid stage; deterministic.
+// results move as coalesced words, and the lanes' loads fall into the warp's
+// contiguous range.  Each thread reads its segment's 16-byte aligned body as
+// 16-byte vectors (UNROLL per step, cached in L1: a lane's next vector and
+// its neighbours' share the lines) and the elements before and after it
+// singly.  Memory-pipeline wavefronts, not bytes, bound the form: one
+// vector load replaces 16 / element-size scalar ones.  For very short
+// segments only: a thread walks its segment alone.  No grid stage;
+// deterministic.
 template <int DT, bool COMP, int UNROLL>
 __global__ void __launch_bounds__(512) seg_lane_kernel(const SegParams p) {
     using A = typename Acc<DT, COMP>::T;
+    constexpr int EB = SegElem<DT>::v;
+    constexpr int VB = 16;
+    constexpr int PV = VB / EB;  // elements per vector
+    constexpr int W = VB / 4;    // 32-bit words per vector
     grid_dependency_wait();
     allow_dependents();
     if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(p.x);
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += T) {
         const int64_t s0 = __ldg(p.offsets + s);
         const int64_t s1 = __ldg(p.offsets + s + 1);
-        A acc[UNROLL];
+        int64_t a0 = s0 + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0 * EB) % VB) % VB) / EB);
+        if (a0 > s1) a0 = s1;
+        const int64_t nv = (s1 - a0) / PV;
+        const int64_t a1 = a0 + nv * PV;
+        A edge = Op<A>::zero();  // head [s0, a0) and tail [a1, s1), fewer than PV each
+        for (int64_t i = s0; i < a0; ++i) acc_elem<DT>(edge, p.x, i);
+        for (int64_t i = a1; i < s1; ++i) acc_elem<DT>(edge, p.x, i);
+        A acc[W];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) acc[u] = Op<A>::zero();
-        int64_t i = s0;
-        for (; i + UNROLL <= s1; i += UNROLL) {
+        for (int q = 0; q < W; ++q) acc[q] = Op<A>::zero();
+        const unsigned char* body = p.x + a0 * EB;
+        int64_t v = 0;
+        for (; v + UNROLL <= nv; v += UNROLL) {
+            uint32_t r[UNROLL][W];
 #pragma unroll
-            for (int u = 0; u < UNROLL; ++u) acc_elem<DT>(acc[u], p.x, i + u);
+            for (int u = 0; u < UNROLL; ++u) ldg_vec_l1(body + (v + u) * VB, r[u]);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+#pragma unroll
+                for (int q = 0; q < W; ++q) acc_word<DT>(acc[q], r[u][q]);
+            }
         }
+        for (; v < nv; ++v) {
+            uint32_t r[W];
+            ldg_vec_l1(body + v * VB, r);
 #pragma unroll
-        for (int u = 0; u + 1 < UNROLL; ++u)
-            if (i + u < s1) acc_elem<DT>(acc[u], p.x, i + u);
-        seg_out(p, s, sum_words<A, UNROLL>(acc));
+            for (int q = 0; q < W; ++q) acc_word<DT>(acc[q], r[q]);
+        }
+        seg_out(p, s, Op<A>::add(sum_words<A, W>(acc), edge));
     }
 }
 

@@ -185,21 +185,23 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
 
 // Measured at ~2^28 FP32 elements (U[-1,1]) against every form:
 //  - 16M segments of 16 elements: one thread per segment (SR_F_LANE_SEGMENTS)
-//    453 us, the dense kernel 711, one warp per segment 2050;
-//  - 4M of 64: one warp per segment (pairs, 16 B x 2) 515 us, dense 610;
-//  - 1M of 268: warp 204 us, 1.6x the best flat-split form; 4M lognormal of
-//    median 40 (empty ones included): warp 602 us, 1.6x;
+//    184 us, the dense kernel 711, one warp per segment 2050;
+//  - 4M of 64: thread 226 us, warp (pairs, 16 B x 2) 515, dense 610;
+//  - 1M of 268: warp 204 us, thread 208, the best flat-split form 328;
+//  - 4M lognormal of median 40 (empty ones included): warp 602 us, thread
+//    991, flat split 973;
 //  - 10^4-10^5 lognormal segments: the flat split (LDG below 32,768
-//    segments, the TMA ring above); the whole-segment forms are 15-800x
+//    segments, the TMA ring above); the whole-segment forms are 15-500x
 //    slower there, one warp or thread holding a segment of millions.
 // The dense kernel (a warp-wide pass over rows with many segment ends) is
 // 1.4-5.5x the plain kernel on uniformly short segments of fewer segments.
 // The rule keeps each form inside the range it was measured in: the thread
-// form for uniform segments of at most 64 bytes with none above 4x the mean;
-// the dense kernel up to 128 bytes (uniform); the warp form for 2^19 or more
-// segments none of which exceeds twice a warp's even share of the elements
-// (32 resident warps per SM, its occupancy at its default shape); the dense
-// kernel up to 512 bytes (uniform); else the plain form.
+// form for 2^19 or more uniform segments of at most 512 bytes with none
+// above 4x the mean; the dense kernel up to 128 bytes (uniform); the warp
+// form for 2^19 or more segments none of which exceeds twice a warp's even
+// share of the elements (32 resident warps per SM, its occupancy at its
+// default shape); the dense kernel up to 512 bytes (uniform); else the
+// plain form.
 int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean, double len_std, double len_max) {
     if (dtype < SR_F32 || dtype > SR_FP8E4M3) return -SR_ERR_DTYPE;
     if (sms < 1 || nseg < 0 || !(len_mean >= 0.0) || !(len_std >= 0.0) || len_max != len_max) return -SR_ERR_ARG;
@@ -207,7 +209,7 @@ int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean,
     const bool uniform = len_std <= 0.5 * len_mean;
     const bool many = nseg >= (int64_t)1 << 19;
     const double longest = len_max > 0.0 ? len_max : len_mean + 4.0 * len_std;
-    if (many && bytes <= 64.0 && uniform && longest <= 4.0 * len_mean) return SR_F_LANE_SEGMENTS;
+    if (many && bytes <= 512.0 && uniform && longest <= 4.0 * len_mean) return SR_F_LANE_SEGMENTS;
     if (bytes <= 128.0 && uniform) return SR_F_DENSE_SEGMENTS;
     const double share = len_mean * (double)nseg / (32.0 * (double)sms);
     if (many && longest <= 2.0 * share) return SR_F_WARP_SEGMENTS;

@@ -236,25 +236,29 @@ def test_host_entry_rejects_without_gpu(lib):
 def test_segmented_layout_flags_without_gpu(lib):
     """The selected segmented path's form rule, a pure host function."""
     f = sr.segmented_layout_flags
+    M = 1 << 20  # "many" segments (the whole-segment forms need 2^19 or more)
+    # fewer segments: the dense kernel for uniformly short ones, else the plain form
     assert f(152, sr.F32, 20_000, 24.0, 0.0, 24.0) == sr.F_DENSE_SEGMENTS       # 96 bytes, uniform
     assert f(152, sr.F32, 20_000, 128.0, 64.0, 0.0) == sr.F_DENSE_SEGMENTS      # 512 bytes, std = mean / 2
     assert f(152, sr.F32, 20_000, 129.0, 0.0, 129.0) == 0                      # just over 512 bytes
     assert f(152, sr.FP8E4M3, 20_000, 512.0, 0.0, 512.0) == sr.F_DENSE_SEGMENTS  # bytes, not elements
-    assert f(152, sr.F32, 1 << 20, 24.0, 20.0, 400.0) == sr.F_WARP_SEGMENTS    # spread: not dense
-    assert f(152, sr.F32, 1 << 22, 64.0, 0.0, 64.0) == sr.F_WARP_SEGMENTS      # 256 bytes: warp before dense
-    assert f(152, sr.F32, 1 << 22, 32.0, 0.0, 32.0) == sr.F_DENSE_SEGMENTS     # 128 bytes: dense first
-    assert f(152, sr.F32, 1 << 24, 16.0, 0.0, 16.0) == sr.F_LANE_SEGMENTS      # 64 bytes, many: a thread each
-    assert f(152, sr.F32, 1 << 24, 16.0, 4.0, 65.0) == sr.F_DENSE_SEGMENTS     # one segment above 4x the mean
-    assert f(152, sr.F32, 1 << 18, 16.0, 0.0, 16.0) == sr.F_DENSE_SEGMENTS     # too few for the thread form
-    assert f(152, sr.F32, 1 << 24, 17.0, 0.0, 17.0) == sr.F_DENSE_SEGMENTS     # 68 bytes
-    assert f(152, sr.F32, 1_000_000, 268.0, 0.0, 268.0) == sr.F_WARP_SEGMENTS
+    assert f(152, sr.F32, (1 << 19) - 1, 16.0, 0.0, 16.0) == sr.F_DENSE_SEGMENTS
+    assert f(152, sr.F32, 10_000, 26843.5, 80000.0, 1 << 24) == 0               # the 10,000-segment batch
+    # many uniform segments up to 512 bytes, none above 4x the mean: a thread each
+    assert f(152, sr.F32, 1 << 24, 16.0, 0.0, 16.0) == sr.F_LANE_SEGMENTS
+    assert f(152, sr.F32, 1 << 22, 64.0, 0.0, 64.0) == sr.F_LANE_SEGMENTS
+    assert f(152, sr.F32, M, 128.0, 64.0, 256.0) == sr.F_LANE_SEGMENTS
+    assert f(152, sr.BF16, M, 256.0, 0.0, 256.0) == sr.F_LANE_SEGMENTS
+    assert f(152, sr.F32, 1 << 24, 16.0, 4.0, 65.0) == sr.F_DENSE_SEGMENTS     # one above 4x the mean
+    assert f(152, sr.F32, M, 16.0, 9.0, 30.0) == sr.F_WARP_SEGMENTS            # spread: neither
+    # many segments, no segment above twice a warp's share: a warp each
+    assert f(152, sr.F32, 1_000_000, 268.0, 0.0, 268.0) == sr.F_WARP_SEGMENTS   # 1072 bytes
     assert f(152, sr.F32, (1 << 19) - 1, 268.0, 0.0, 268.0) == 0               # too few segments
     share = 268.0 * 1_000_000 / (32 * 152)
-    assert f(152, sr.F32, 1_000_000, 268.0, 50.0, 2 * share) == sr.F_WARP_SEGMENTS
-    assert f(152, sr.F32, 1_000_000, 268.0, 50.0, 2 * share + 1) == 0          # one segment too long
+    assert f(152, sr.F32, 1_000_000, 268.0, 150.0, 2 * share) == sr.F_WARP_SEGMENTS
+    assert f(152, sr.F32, 1_000_000, 268.0, 150.0, 2 * share + 1) == 0          # one segment too long
     assert f(152, sr.F32, 1_000_000, 268.0, 20000.0, 0.0) == sr.F_WARP_SEGMENTS  # unknown max: mean + 4 std
     assert f(152, sr.F32, 1_000_000, 268.0, 40000.0, 0.0) == 0
-    assert f(152, sr.F32, 10_000, 26843.5, 80000.0, 1 << 24) == 0               # the 10,000-segment batch
     for bad in ((0, sr.F32, 10, 1.0, 0.0, 1.0), (152, sr.F32, -1, 1.0, 0.0, 1.0),
                 (152, sr.F32, 10, float("nan"), 0.0, 1.0), (152, sr.F32, 10, 1.0, -1.0, 1.0)):
         with pytest.raises(sr.SRError) as e:

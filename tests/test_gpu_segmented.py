@@ -390,6 +390,16 @@ def test_warp_segments_plan_and_determinism(sr):
     for form in (WARP, LANE):
         outs = [sr.reduce_sum_segmented(xd, od, variant=form | st).cpu().numpy() for st in STAGES]
         assert all(np.array_equal(outs[0], o) for o in outs[1:])   # same kernel, same order, any stage bits
+        # captured once into a library-owned graph: replays give the same results
+        out = torch.full((off.size - 1,), -1.0, dtype=torch.float32, device="cuda")
+        g = sr.SegmentedGraph(xd, od, out, sr.make_config(form | sr.ATOMIC))
+        for _ in range(3):
+            out.fill_(-1.0)
+            g.launch()
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), outs[0])
+        g.close()
+    assert sr.stream_status() == sr.OK
 
 
 @pytest.mark.parametrize("stage", STAGES)
