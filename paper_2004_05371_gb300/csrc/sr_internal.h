@@ -29,7 +29,7 @@ struct Workspace {
     int* err = nullptr;
     unsigned char* partials = nullptr;
     unsigned char* seg = nullptr;
-    int* check = nullptr;  // verdict of the checked segmented entry (header byte 160)
+    int* check = nullptr;  // result of the checked segmented entry's offsets check (header byte 160)
 };
 
 struct DeviceInfo {
