@@ -601,6 +601,80 @@ inline const void* pick_seg_tma(int vec, int unroll) {
     return vec == 16 ? pick_seg_bulk<DT, COMP, 16>(unroll) : (vec == 32 ? pick_seg_bulk<DT, COMP, 32>(unroll) : nullptr);
 }
 
+// ------------------------------------------------ lane-per-segment form
+// One thread sums x[s0, s1) alone: the 16-byte aligned body as 16-byte
+// vectors (UNROLL per step, cached in L1: a lane's next vector and its
+// neighbours' share the lines), the elements before and after it singly.
+template <int DT, bool COMP, int UNROLL>
+__device__ __forceinline__ typename Acc<DT, COMP>::T lane_sum(const unsigned char* x, int64_t s0, int64_t s1) {
+    using A = typename Acc<DT, COMP>::T;
+    constexpr int EB = SegElem<DT>::v;
+    constexpr int VB = 16;
+    constexpr int PV = VB / EB;  // elements per vector
+    constexpr int W = VB / 4;    // 32-bit words per vector
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x);
+    int64_t a0 = s0 + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0 * EB) % VB) % VB) / EB);
+    if (a0 > s1) a0 = s1;
+    const int64_t nv = (s1 - a0) / PV;
+    const int64_t a1 = a0 + nv * PV;
+    A edge = Op<A>::zero();  // head [s0, a0) and tail [a1, s1), fewer than PV each
+    for (int64_t i = s0; i < a0; ++i) acc_elem<DT>(edge, x, i);
+    for (int64_t i = a1; i < s1; ++i) acc_elem<DT>(edge, x, i);
+    A acc[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[q] = Op<A>::zero();
+    const unsigned char* body = x + a0 * EB;
+    int64_t v = 0;
+    for (; v + UNROLL <= nv; v += UNROLL) {
+        uint32_t r[UNROLL][W];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) ldg_vec_l1(body + (v + u) * VB, r[u]);
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) acc_word<DT>(acc[q], r[u][q]);
+        }
+    }
+    for (; v < nv; ++v) {
+        uint32_t r[W];
+        ldg_vec_l1(body + v * VB, r);
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc_word<DT>(acc[q], r[q]);
+    }
+    return Op<A>::add(sum_words<A, W>(acc), edge);
+}
+
+// SR_F_LANE_SEGMENTS: thread t of the grid sums segments t, t + T, ... alone
+// (T threads), so a warp covers 32 consecutive segments: the offsets and the
+// results move as coalesced words, and the lanes' loads fall into the warp's
+// contiguous range.  One vector load replaces 16 / element-size scalar
+// ones, which cut the time at 16-element segments 2.5-fold.  For very short
+// segments only: a thread walks its segment alone.  No grid stage;
+// deterministic.
+template <int DT, bool COMP, int UNROLL>
+__global__ void __launch_bounds__(512) seg_lane_kernel(const SegParams p) {
+    grid_dependency_wait();
+    allow_dependents();
+    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += T) {
+        const int64_t s0 = __ldg(p.offsets + s);
+        const int64_t s1 = __ldg(p.offsets + s + 1);
+        seg_out(p, s, lane_sum<DT, COMP, UNROLL>(p.x, s0, s1));
+    }
+}
+
+template <int DT, bool COMP>
+inline const void* pick_seg_lane(int unroll) {
+    switch (unroll) {
+    case 1: return (const void*)seg_lane_kernel<DT, COMP, 1>;
+    case 2: return (const void*)seg_lane_kernel<DT, COMP, 2>;
+    case 4: return (const void*)seg_lane_kernel<DT, COMP, 4>;
+    case 8: return (const void*)seg_lane_kernel<DT, COMP, 8>;
+    default: return nullptr;
+    }
+}
+
 // ------------------------------------------------ warp-per-segment form
 // SR_F_WARP_SEGMENTS: each warp sums whole segments, so no segment crosses a
 // warp and there is no grid stage (results are deterministic).  Warps take
@@ -611,7 +685,12 @@ inline const void* pick_seg_tma(int vec, int unroll) {
 // by the first lanes; the vectors between are spread over the lanes, UNROLL
 // per lane and batch; then one warp reduction and one store.  Segments go in
 // pairs: both first batches are loaded before either is summed, so each warp
-// keeps two segments' loads in flight.
+// keeps two segments' loads in flight.  A segment of at most kLaneAloneBytes
+// is summed by its own lane instead (lane_sum), all such segments of a block
+// at once: skewed layouts, mostly short segments with a long tail, pay the
+// warp-wide path only for the long ones.
+constexpr int64_t kLaneAloneBytes = 512;  // segments a lane of the warp form sums alone
+
 template <int DT, bool COMP, int VB, int UNROLL>
 __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
     using A = typename Acc<DT, COMP>::T;
@@ -632,14 +711,26 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
         const int64_t i = b0 + (lane < nb ? lane : nb);           // lane nb (or 31) holds the end
         const int64_t o = __ldg(p.offsets + i);
         const int64_t o_end = __ldg(p.offsets + b0 + nb);
-        // two segments per step: both first batches of loads are in flight together
-        for (int k = 0; k < (int)nb; k += 2) {
-            const bool two = k + 1 < (int)nb;  // warp-uniform
+        // this lane's segment [o, e); the short ones are summed by their lane alone
+        const int64_t o_up = __shfl_down_sync(0xffffffffu, o, 1);
+        const bool mine = lane < nb;
+        const int64_t e = (lane + 1 < nb) ? o_up : o_end;
+        const bool alone = mine && (e - o) * EB <= kLaneAloneBytes;
+        if (alone) seg_out(p, b0 + lane, lane_sum<DT, COMP, 4>(p.x, o, e));
+        // the rest by the whole warp, two at a time: both first batches of loads in flight together
+        unsigned todo = __ballot_sync(0xffffffffu, mine && !alone);
+        while (todo != 0u) {
+            const int k0 = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const bool two = todo != 0u;  // warp-uniform
+            const int k1 = two ? __ffs(todo) - 1 : k0;
+            if (two) todo &= todo - 1u;
             int64_t s0[2], s1[2];
-            s0[0] = __shfl_sync(0xffffffffu, o, k);
-            s1[0] = two ? __shfl_sync(0xffffffffu, o, k + 1) : o_end;
-            s0[1] = s1[0];
-            s1[1] = !two ? s1[0] : ((k + 2 < (int)nb) ? __shfl_sync(0xffffffffu, o, k + 2) : o_end);
+            s0[0] = __shfl_sync(0xffffffffu, o, k0);
+            s1[0] = __shfl_sync(0xffffffffu, e, k0);
+            s0[1] = __shfl_sync(0xffffffffu, o, k1);
+            s1[1] = __shfl_sync(0xffffffffu, e, k1);
+            if (!two) s0[1] = s1[1] = s1[0];  // an empty second segment
             int64_t a0[2], nv[2];
             A edge[2], acc[2][W];
             uint32_t r[2][UNROLL][W];
@@ -689,81 +780,13 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
             const A t0 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[0]), edge[0]));
             const A t1 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[1]), edge[1]));
             if (lane == 0) {
-                seg_out(p, b0 + k, t0);
-                if (two) seg_out(p, b0 + k + 1, t1);
+                seg_out(p, b0 + k0, t0);
+                if (two) seg_out(p, b0 + k1, t1);
             }
         }
     }
 }
 
-// ------------------------------------------------ lane-per-segment form
-// SR_F_LANE_SEGMENTS: thread t of the grid sums segments t, t + T, ... alone
-// (T threads), so a warp covers 32 consecutive segments: the offsets and the
-// results move as coalesced words, and the lanes' loads fall into the warp's
-// contiguous range.  Each thread reads its segment's 16-byte aligned body as
-// 16-byte vectors (UNROLL per step, cached in L1: a lane's next vector and
-// its neighbours' share the lines) and the elements before and after it
-// singly.  Memory-pipeline wavefronts, not bytes, bound the form: one
-// vector load replaces 16 / element-size scalar ones.  For very short
-// segments only: a thread walks its segment alone.  No grid stage;
-// deterministic.
-template <int DT, bool COMP, int UNROLL>
-__global__ void __launch_bounds__(512) seg_lane_kernel(const SegParams p) {
-    using A = typename Acc<DT, COMP>::T;
-    constexpr int EB = SegElem<DT>::v;
-    constexpr int VB = 16;
-    constexpr int PV = VB / EB;  // elements per vector
-    constexpr int W = VB / 4;    // 32-bit words per vector
-    grid_dependency_wait();
-    allow_dependents();
-    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    const uintptr_t xa = reinterpret_cast<uintptr_t>(p.x);
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += T) {
-        const int64_t s0 = __ldg(p.offsets + s);
-        const int64_t s1 = __ldg(p.offsets + s + 1);
-        int64_t a0 = s0 + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0 * EB) % VB) % VB) / EB);
-        if (a0 > s1) a0 = s1;
-        const int64_t nv = (s1 - a0) / PV;
-        const int64_t a1 = a0 + nv * PV;
-        A edge = Op<A>::zero();  // head [s0, a0) and tail [a1, s1), fewer than PV each
-        for (int64_t i = s0; i < a0; ++i) acc_elem<DT>(edge, p.x, i);
-        for (int64_t i = a1; i < s1; ++i) acc_elem<DT>(edge, p.x, i);
-        A acc[W];
-#pragma unroll
-        for (int q = 0; q < W; ++q) acc[q] = Op<A>::zero();
-        const unsigned char* body = p.x + a0 * EB;
-        int64_t v = 0;
-        for (; v + UNROLL <= nv; v += UNROLL) {
-            uint32_t r[UNROLL][W];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) ldg_vec_l1(body + (v + u) * VB, r[u]);
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-#pragma unroll
-                for (int q = 0; q < W; ++q) acc_word<DT>(acc[q], r[u][q]);
-            }
-        }
-        for (; v < nv; ++v) {
-            uint32_t r[W];
-            ldg_vec_l1(body + v * VB, r);
-#pragma unroll
-            for (int q = 0; q < W; ++q) acc_word<DT>(acc[q], r[q]);
-        }
-        seg_out(p, s, Op<A>::add(sum_words<A, W>(acc), edge));
-    }
-}
-
-template <int DT, bool COMP>
-inline const void* pick_seg_lane(int unroll) {
-    switch (unroll) {
-    case 1: return (const void*)seg_lane_kernel<DT, COMP, 1>;
-    case 2: return (const void*)seg_lane_kernel<DT, COMP, 2>;
-    case 4: return (const void*)seg_lane_kernel<DT, COMP, 4>;
-    case 8: return (const void*)seg_lane_kernel<DT, COMP, 8>;
-    default: return nullptr;
-    }
-}
 
 template <int DT, bool COMP, int VB>
 inline const void* pick_seg_warp_u(int unroll) {
