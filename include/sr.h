@@ -106,13 +106,14 @@ typedef enum {
                                    reduction and one store per segment).  No segment
                                    crosses a warp, so the grid stage is not used and
                                    nothing is zeroed or finished; deterministic.  For
-                                   many segments of similar length: a long segment is
-                                   summed by one warp alone.  Segments go in pairs,
+                                   many segments with no very long one: a long segment
+                                   is summed by one warp alone.  Segments go in pairs,
                                    both first batches of loads in flight together; a
                                    batch is `unroll` 16/32-byte vectors per lane
-                                   (default 16 bytes x 2; unroll 1/2/4/8).  Not with
-                                   SR_F_BULK or SR_F_DENSE_SEGMENTS
-                                   (SR_ERR_UNSUPPORTED). */
+                                   (default 16 bytes x 2; unroll 1/2/4/8).  Segments of
+                                   at most 512 bytes are summed by a single lane.  Not
+                                   with another form flag (SR_ERR_UNSUPPORTED).  The
+                                   paper has no counterpart. */
 #define SR_F_LANE_SEGMENTS 0x8000 /* segmented only: each thread sums whole segments
                                    alone (thread t takes segments t, t + T, ...), so a
                                    warp covers 32 consecutive segments with coalesced
@@ -120,7 +121,7 @@ typedef enum {
                                    segment's aligned body, `unroll` (1/2/4/8, default 4)
                                    per step.  For very short segments.  No grid stage;
                                    deterministic.  Not with another form flag
-                                   (SR_ERR_UNSUPPORTED). */
+                                   (SR_ERR_UNSUPPORTED).  The paper has no counterpart. */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses
@@ -492,7 +493,8 @@ int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int d
  * segments none longer than twice a warp's even share of the elements
  * (2 * mean * nseg / (32 * sms)); SR_F_DENSE_SEGMENTS for uniformly short
  * segments (<= 512 bytes, std <= mean / 2); else 0 (the plain form).
- * Host-only and pure (no device call).
+ * Host-only and pure (no device call).  The paper has no counterpart: the
+ * thresholds come from this library's own measurements of the forms.
  * Returns the flag, or a negated status: -SR_ERR_DTYPE, -SR_ERR_ARG (sms < 1,
  * nseg < 0, negative or NaN statistics). */
 int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean, double len_std, double len_max);
