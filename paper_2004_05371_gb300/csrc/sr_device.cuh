@@ -41,11 +41,6 @@ __device__ __forceinline__ void ldg_vec(const void* p, uint32_t (&r)[8]) {
           "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "l"(p));
 }
-// Read-only 16-byte load that allocates in L1: for access patterns in which
-// neighbouring lanes, or a lane's next load, use the rest of the line.
-__device__ __forceinline__ void ldg_vec_l1(const void* p, uint32_t (&r)[4]) {
-    asm("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(p));
-}
 __device__ __forceinline__ void lds_vec(uint32_t saddr, uint32_t (&r)[4]) {
     asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])

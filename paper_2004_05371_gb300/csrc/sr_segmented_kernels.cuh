@@ -602,6 +602,12 @@ inline const void* pick_seg_tma(int vec, int unroll) {
 }
 
 // ------------------------------------------------ lane-per-segment form
+// Read-only 16-byte load that allocates in L1: for access patterns in which
+// neighbouring lanes, or a lane's next load, use the rest of the line.
+__device__ __forceinline__ void ldg_vec_l1(const void* p, uint32_t (&r)[4]) {
+    asm("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(p));
+}
+
 // One thread sums x[s0, s1) alone: the 16-byte aligned body as 16-byte
 // vectors (UNROLL per step, cached in L1: a lane's next vector and its
 // neighbours' share the lines), the elements before and after it singly.
