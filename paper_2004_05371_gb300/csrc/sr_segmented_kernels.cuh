@@ -766,19 +766,29 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
                         for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[j][u][q]);
                     }
                 }
-                // the rest of a segment longer than one batch
-                const unsigned char* body = p.x + a0[j] * EB;
-                for (int64_t v0 = 32 * UNROLL; v0 < nv[j]; v0 += 32 * UNROLL) {
+            }
+            // the rest of a segment longer than one batch, with both batch
+            // buffers free now: 2 * UNROLL vectors per lane in flight
 #pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        const int64_t v = v0 + u * 32 + lane;
-                        if (v < nv[j]) ldg_vec(body + v * VB, r[0][u]);
+            for (int j = 0; j < 2; ++j) {
+                const unsigned char* body = p.x + a0[j] * EB;
+                for (int64_t v0 = 32 * UNROLL; v0 < nv[j]; v0 += 64 * UNROLL) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                        for (int u = 0; u < UNROLL; ++u) {
+                            const int64_t v = v0 + (h * UNROLL + u) * 32 + lane;
+                            if (v < nv[j]) ldg_vec(body + v * VB, r[h][u]);
+                        }
                     }
 #pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        if (v0 + u * 32 + lane < nv[j]) {
+                    for (int h = 0; h < 2; ++h) {
 #pragma unroll
-                            for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[0][u][q]);
+                        for (int u = 0; u < UNROLL; ++u) {
+                            if (v0 + (h * UNROLL + u) * 32 + lane < nv[j]) {
+#pragma unroll
+                                for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[h][u][q]);
+                            }
                         }
                     }
                 }

@@ -187,11 +187,11 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
 //  - 16M segments of 16 elements: one thread per segment (SR_F_LANE_SEGMENTS)
 //    184 us, the dense kernel 711, one warp per segment 206;
 //  - 4M of 64: thread 226 us, warp 229, dense 610;
-//  - 1M of 268: warp 213 us, thread 208, the best flat-split form 328;
-//  - 4M lognormal of median 40 (empty ones included): warp 318 us (its
+//  - 1M of 268: warp 211 us, thread 208, the best flat-split form 328;
+//  - 4M lognormal of median 40 (empty ones included): warp 284 us (its
 //    short segments summed by single lanes), thread 991, flat split 973;
 //  - 10^4-10^5 lognormal segments: the flat split (LDG below 32,768
-//    segments, the TMA ring above); the whole-segment forms are 15-500x
+//    segments, the TMA ring above); the whole-segment forms are 13-500x
 //    slower there, one warp or thread holding a segment of millions.
 // The dense kernel (a warp-wide pass over rows with many segment ends) is
 // 1.4-5.5x the plain kernel on uniformly short segments of fewer segments.
