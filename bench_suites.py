@@ -399,7 +399,8 @@ def seglayouts_suite(args):
     forms = {"ldg256": ((256, 32, 8), 0), "dense256": ((256, 32, 8), sr.F_DENSE_SEGMENTS),
              "ldg512": ((512, 32, 4), 0), "dense512": ((512, 32, 4), sr.F_DENSE_SEGMENTS),
              "tma": ((256, 32, 4), sr.F_BULK), "warp16": ((256, 16, 4), sr.F_WARP_SEGMENTS),
-             "warp16u2": ((256, 16, 2), sr.F_WARP_SEGMENTS), "lane": ((256, 16, 4), sr.F_LANE_SEGMENTS)}
+             "warp16u2": ((256, 16, 2), sr.F_WARP_SEGMENTS), "lane": ((256, 16, 4), sr.F_LANE_SEGMENTS),
+             "lane32": ((256, 32, 4), sr.F_LANE_SEGMENTS)}
     only = getattr(args, "layout", None)
     form = getattr(args, "seg_form", None)
     for name, off in cases:

@@ -117,9 +117,9 @@ typedef enum {
 #define SR_F_LANE_SEGMENTS 0x8000 /* segmented only: each thread sums whole segments
                                    alone (thread t takes segments t, t + T, ...), so a
                                    warp covers 32 consecutive segments with coalesced
-                                   offsets and results; 16-byte vector loads of each
-                                   segment's aligned body, `unroll` (1/2/4/8, default 4)
-                                   per step.  For very short segments.  No grid stage;
+                                   offsets and results; vector loads of each segment's
+                                   aligned body (vec_bytes 16/32, default 16), `unroll`
+                                   (1/2/4/8, default 4) per step.  For very short segments.  No grid stage;
                                    deterministic.  Not with another form flag
                                    (SR_ERR_UNSUPPORTED).  The paper has no counterpart. */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
@@ -480,14 +480,15 @@ int sr_selector_choose(sr_selector selector, int64_t n, int dtype, int64_t nseg,
  * applies the form sr_segmented_layout_flags gives for them: it adds
  * SR_F_DENSE_SEGMENTS to the chosen configuration, or replaces the chosen
  * configuration's shape with SR_F_WARP_SEGMENTS or SR_F_LANE_SEGMENTS at its
- * default shape. */
+ * default shape (the lane form with 32-byte vectors from 128 bytes per
+ * segment on average). */
 int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int dtype, void* out,
                            sr_stream_t stream);
 /* The segmented form for a layout, from the caller's segment-length
  * statistics (mean, standard deviation, maximum; len_max <= 0 when unknown,
  * then mean + 4 std stands in) and the device's SM count, in this order:
  * SR_F_LANE_SEGMENTS for 2^19 or more uniform segments (std <= mean / 2) of
- * at most 512 bytes on average and none above 4x the mean;
+ * at most 1 KiB on average and none above 4x the mean;
  * SR_F_DENSE_SEGMENTS for uniformly very short segments (mean * element size
  * <= 128 bytes, std <= mean / 2); SR_F_WARP_SEGMENTS for 2^19 or more
  * segments none longer than twice a warp's even share of the elements

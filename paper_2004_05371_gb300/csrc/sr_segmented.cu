@@ -40,7 +40,7 @@ bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, bool bul
     const void* (*den)(bool, int, int) = nullptr;
     const void* (*tma)(bool, int, int) = nullptr;
     const void* (*wrp)(bool, int, int) = nullptr;
-    const void* (*lan)(bool, int) = nullptr;
+    const void* (*lan)(bool, int, int) = nullptr;
     switch (dtype) {
     case SR_F32: ldg = seg_ldg_f32; den = seg_dense_f32; tma = seg_tma_f32; wrp = seg_warp_f32; lan = seg_lane_f32; break;
     case SR_I32: ldg = seg_ldg_i32; den = seg_dense_i32; tma = seg_tma_i32; wrp = seg_warp_i32; lan = seg_lane_i32; break;
@@ -54,7 +54,7 @@ bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, bool bul
     }
     if (warp || lane) {  // one kernel, nothing to finish
         *fin = nullptr;
-        *main = (dense || bulk || (warp && lane)) ? nullptr : (warp ? wrp(comp, vec, unroll) : lan(comp, unroll));
+        *main = (dense || bulk || (warp && lane)) ? nullptr : (warp ? wrp(comp, vec, unroll) : lan(comp, vec, unroll));
         return *main != nullptr;
     }
     const void* plain = ldg(comp, vec, unroll, fin);  // also sets the second kernel
@@ -111,7 +111,7 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
     p.dense = (c.variant & SR_F_DENSE_SEGMENTS) != 0;
     p.warp = (c.variant & SR_F_WARP_SEGMENTS) != 0;
     p.lane = (c.variant & SR_F_LANE_SEGMENTS) != 0;
-    if (p.lane) {  // element loads: vec_bytes plays no part
+    if (p.lane) {  // 16-byte vectors, 4 per step
         p.vec = c.vec_bytes ? c.vec_bytes : 16;
         p.unroll = c.unroll ? c.unroll : 4;
     }

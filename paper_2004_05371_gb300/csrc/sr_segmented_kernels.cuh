@@ -607,15 +607,19 @@ inline const void* pick_seg_tma(int vec, int unroll) {
 __device__ __forceinline__ void ldg_vec_l1(const void* p, uint32_t (&r)[4]) {
     asm("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(p));
 }
+__device__ __forceinline__ void ldg_vec_l1(const void* p, uint32_t (&r)[8]) {
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
+}
 
-// One thread sums x[s0, s1) alone: the 16-byte aligned body as 16-byte
+// One thread sums x[s0, s1) alone: the VB-byte aligned body as VB-byte
 // vectors (UNROLL per step, cached in L1: a lane's next vector and its
 // neighbours' share the lines), the elements before and after it singly.
-template <int DT, bool COMP, int UNROLL>
+template <int DT, bool COMP, int VB, int UNROLL>
 __device__ __forceinline__ typename Acc<DT, COMP>::T lane_sum(const unsigned char* x, int64_t s0, int64_t s1) {
     using A = typename Acc<DT, COMP>::T;
     constexpr int EB = SegElem<DT>::v;
-    constexpr int VB = 16;
     constexpr int PV = VB / EB;  // elements per vector
     constexpr int W = VB / 4;    // 32-bit words per vector
     const uintptr_t xa = reinterpret_cast<uintptr_t>(x);
@@ -657,7 +661,7 @@ __device__ __forceinline__ typename Acc<DT, COMP>::T lane_sum(const unsigned cha
 // ones, which cut the time at 16-element segments 2.5-fold.  For very short
 // segments only: a thread walks its segment alone.  No grid stage;
 // deterministic.
-template <int DT, bool COMP, int UNROLL>
+template <int DT, bool COMP, int VB, int UNROLL>
 __global__ void __launch_bounds__(512) seg_lane_kernel(const SegParams p) {
     grid_dependency_wait();
     allow_dependents();
@@ -666,19 +670,23 @@ __global__ void __launch_bounds__(512) seg_lane_kernel(const SegParams p) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += T) {
         const int64_t s0 = __ldg(p.offsets + s);
         const int64_t s1 = __ldg(p.offsets + s + 1);
-        seg_out(p, s, lane_sum<DT, COMP, UNROLL>(p.x, s0, s1));
+        seg_out(p, s, lane_sum<DT, COMP, VB, UNROLL>(p.x, s0, s1));
     }
 }
 
-template <int DT, bool COMP>
-inline const void* pick_seg_lane(int unroll) {
+template <int DT, bool COMP, int VB>
+inline const void* pick_seg_lane_u(int unroll) {
     switch (unroll) {
-    case 1: return (const void*)seg_lane_kernel<DT, COMP, 1>;
-    case 2: return (const void*)seg_lane_kernel<DT, COMP, 2>;
-    case 4: return (const void*)seg_lane_kernel<DT, COMP, 4>;
-    case 8: return (const void*)seg_lane_kernel<DT, COMP, 8>;
+    case 1: return (const void*)seg_lane_kernel<DT, COMP, VB, 1>;
+    case 2: return (const void*)seg_lane_kernel<DT, COMP, VB, 2>;
+    case 4: return (const void*)seg_lane_kernel<DT, COMP, VB, 4>;
+    case 8: return (const void*)seg_lane_kernel<DT, COMP, VB, 8>;
     default: return nullptr;
     }
+}
+template <int DT, bool COMP>
+inline const void* pick_seg_lane(int vec, int unroll) {
+    return vec == 16 ? pick_seg_lane_u<DT, COMP, 16>(unroll) : (vec == 32 ? pick_seg_lane_u<DT, COMP, 32>(unroll) : nullptr);
 }
 
 // ------------------------------------------------ warp-per-segment form
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
         const bool mine = lane < nb;
         const int64_t e = (lane + 1 < nb) ? o_up : o_end;
         const bool alone = mine && (e - o) * EB <= kLaneAloneBytes;
-        if (alone) seg_out(p, b0 + lane, lane_sum<DT, COMP, 4>(p.x, o, e));
+        if (alone) seg_out(p, b0 + lane, lane_sum<DT, COMP, 16, 4>(p.x, o, e));
         // the rest by the whole warp, two at a time: both first batches of loads in flight together
         unsigned todo = __ballot_sync(0xffffffffu, mine && !alone);
         while (todo != 0u) {

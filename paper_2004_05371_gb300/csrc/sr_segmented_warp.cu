@@ -16,17 +16,17 @@ const void* seg_warp_bf16(bool comp, int vec, int unroll) {
 const void* seg_warp_fp8(bool comp, int vec, int unroll) {
     return comp ? pick_seg_warp<kDtFP8, true>(vec, unroll) : pick_seg_warp<kDtFP8, false>(vec, unroll);
 }
-const void* seg_lane_f32(bool comp, int unroll) {
-    return comp ? pick_seg_lane<kDtF32, true>(unroll) : pick_seg_lane<kDtF32, false>(unroll);
+const void* seg_lane_f32(bool comp, int vec, int unroll) {
+    return comp ? pick_seg_lane<kDtF32, true>(vec, unroll) : pick_seg_lane<kDtF32, false>(vec, unroll);
 }
-const void* seg_lane_i32(bool comp, int unroll) {
+const void* seg_lane_i32(bool comp, int vec, int unroll) {
     (void)comp;  // integer sums are exact
-    return pick_seg_lane<kDtI32, false>(unroll);
+    return pick_seg_lane<kDtI32, false>(vec, unroll);
 }
-const void* seg_lane_bf16(bool comp, int unroll) {
-    return comp ? pick_seg_lane<kDtBF16, true>(unroll) : pick_seg_lane<kDtBF16, false>(unroll);
+const void* seg_lane_bf16(bool comp, int vec, int unroll) {
+    return comp ? pick_seg_lane<kDtBF16, true>(vec, unroll) : pick_seg_lane<kDtBF16, false>(vec, unroll);
 }
-const void* seg_lane_fp8(bool comp, int unroll) {
-    return comp ? pick_seg_lane<kDtFP8, true>(unroll) : pick_seg_lane<kDtFP8, false>(unroll);
+const void* seg_lane_fp8(bool comp, int vec, int unroll) {
+    return comp ? pick_seg_lane<kDtFP8, true>(vec, unroll) : pick_seg_lane<kDtFP8, false>(vec, unroll);
 }
 }  // namespace sr

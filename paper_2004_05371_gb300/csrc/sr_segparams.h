@@ -49,9 +49,9 @@ const void* seg_warp_i32(bool comp, int vec, int unroll);
 const void* seg_warp_bf16(bool comp, int vec, int unroll);
 const void* seg_warp_fp8(bool comp, int vec, int unroll);
 // The lane-per-segment form, in the same translation unit.
-const void* seg_lane_f32(bool comp, int unroll);
-const void* seg_lane_i32(bool comp, int unroll);
-const void* seg_lane_bf16(bool comp, int unroll);
-const void* seg_lane_fp8(bool comp, int unroll);
+const void* seg_lane_f32(bool comp, int vec, int unroll);
+const void* seg_lane_i32(bool comp, int vec, int unroll);
+const void* seg_lane_bf16(bool comp, int vec, int unroll);
+const void* seg_lane_fp8(bool comp, int vec, int unroll);
 
 }  // namespace sr

@@ -177,6 +177,9 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
     if (form == SR_F_WARP_SEGMENTS || form == SR_F_LANE_SEGMENTS) {  // the form's own shape; no grid stage
         c.variant = (c.variant & ~(SR_F_BULK | SR_F_DENSE_SEGMENTS)) | form;
         c.vec_bytes = c.unroll = c.block_threads = c.stages = c.grid = c.ctas_per_sm = 0;
+        // the lane form with 32-byte vectors from 128 bytes per segment (measured: 16M x 16
+        // FP32 185 us with 16 B against 196; 4M x 64 226 against 179; 1M x 268 208 against 196)
+        if (form == SR_F_LANE_SEGMENTS && len_mean * (double)sr::elem_size(dtype) >= 128.0) c.vec_bytes = 32;
     } else {
         c.variant |= form;
     }
@@ -186,8 +189,9 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
 // Measured at ~2^28 FP32 elements (U[-1,1]) against every form:
 //  - 16M segments of 16 elements: one thread per segment (SR_F_LANE_SEGMENTS)
 //    184 us, the dense kernel 711, one warp per segment 206;
-//  - 4M of 64: thread 226 us, warp 229, dense 610;
-//  - 1M of 268: warp 211 us, thread 208, the best flat-split form 328;
+//  - 4M of 64: thread 179 us (32-byte vectors), warp 229, dense 610;
+//  - 1M of 268: thread 196 us (32-byte vectors), warp 211, the best
+//    flat-split form 328;
 //  - 4M lognormal of median 40 (empty ones included): warp 284 us (its
 //    short segments summed by single lanes), thread 991, flat split 973;
 //  - 10^4-10^5 lognormal segments: the flat split (LDG below 32,768
@@ -196,8 +200,8 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
 // The dense kernel (a warp-wide pass over rows with many segment ends) is
 // 1.4-5.5x the plain kernel on uniformly short segments of fewer segments.
 // The rule keeps each form inside the range it was measured in: the thread
-// form for 2^19 or more uniform segments of at most 512 bytes with none
-// above 4x the mean; the dense kernel up to 128 bytes (uniform); the warp
+// form for 2^19 or more uniform segments of at most 1 KiB with none above 4x
+// the mean; the dense kernel up to 128 bytes (uniform); the warp
 // form for 2^19 or more segments none of which exceeds twice a warp's even
 // share of the elements (32 resident warps per SM, its occupancy at its
 // default shape); the dense kernel up to 512 bytes (uniform); else the
@@ -209,7 +213,7 @@ int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean,
     const bool uniform = len_std <= 0.5 * len_mean;
     const bool many = nseg >= (int64_t)1 << 19;
     const double longest = len_max > 0.0 ? len_max : len_mean + 4.0 * len_std;
-    if (many && bytes <= 512.0 && uniform && longest <= 4.0 * len_mean) return SR_F_LANE_SEGMENTS;
+    if (many && bytes <= 1024.0 && uniform && longest <= 4.0 * len_mean) return SR_F_LANE_SEGMENTS;
     if (bytes <= 128.0 && uniform) return SR_F_DENSE_SEGMENTS;
     const double share = len_mean * (double)nseg / (32.0 * (double)sms);
     if (many && longest <= 2.0 * share) return SR_F_WARP_SEGMENTS;

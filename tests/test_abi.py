@@ -244,11 +244,13 @@ def test_segmented_layout_flags_without_gpu(lib):
     assert f(152, sr.FP8E4M3, 20_000, 512.0, 0.0, 512.0) == sr.F_DENSE_SEGMENTS  # bytes, not elements
     assert f(152, sr.F32, (1 << 19) - 1, 16.0, 0.0, 16.0) == sr.F_DENSE_SEGMENTS
     assert f(152, sr.F32, 10_000, 26843.5, 80000.0, 1 << 24) == 0               # the 10,000-segment batch
-    # many uniform segments up to 512 bytes, none above 4x the mean: a thread each
+    # many uniform segments up to 1 KiB, none above 4x the mean: a thread each
     assert f(152, sr.F32, 1 << 24, 16.0, 0.0, 16.0) == sr.F_LANE_SEGMENTS
     assert f(152, sr.F32, 1 << 22, 64.0, 0.0, 64.0) == sr.F_LANE_SEGMENTS
     assert f(152, sr.F32, M, 128.0, 64.0, 256.0) == sr.F_LANE_SEGMENTS
     assert f(152, sr.BF16, M, 256.0, 0.0, 256.0) == sr.F_LANE_SEGMENTS
+    assert f(152, sr.F32, M, 256.0, 0.0, 256.0) == sr.F_LANE_SEGMENTS          # 1 KiB
+    assert f(152, sr.F32, M, 257.0, 0.0, 257.0) == sr.F_WARP_SEGMENTS          # just over 1 KiB
     assert f(152, sr.F32, 1 << 24, 16.0, 4.0, 65.0) == sr.F_DENSE_SEGMENTS     # one above 4x the mean
     assert f(152, sr.F32, M, 16.0, 9.0, 30.0) == sr.F_WARP_SEGMENTS            # spread: neither
     # many segments, no segment above twice a warp's share: a warp each

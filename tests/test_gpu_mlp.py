@@ -162,32 +162,24 @@ def test_selected_entry_points(sr):
         sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), 20_000, sr.I32, out.data_ptr(),
                                                       24.0, 0.0, 24.0))
         assert np.array_equal(out.cpu().numpy(), oracle.segsum_i32(x, off))
-    # very many mid-length segments: the selected call takes SR_F_WARP_SEGMENTS
+    # very many segments: the selected call takes a whole-segment form
     nseg = 600_000
-    lens = np.random.default_rng(6).integers(50, 401, nseg).astype(np.int64)
-    off = np.zeros(nseg + 1, np.int64)
-    np.cumsum(lens, out=off[1:])
-    assert sr.segmented_layout_flags(sms, sr.I32, nseg, lens.mean(), lens.std(), lens.max()) == sr.F_WARP_SEGMENTS
-    x = workloads.uniform_i32(int(off[-1]), seed=6)
-    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
-    out = torch.zeros(nseg, dtype=torch.int64, device="cuda")
-    ref = oracle.segsum_i32(x, off)
-    for s in (nat, None):
-        out.fill_(-1)
-        sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), nseg, sr.I32, out.data_ptr(),
-                                                      lens.mean(), lens.std(), lens.max()))
-        assert np.array_equal(out.cpu().numpy(), ref)
-    # very many tiny segments: the selected call takes SR_F_LANE_SEGMENTS
-    lens = np.random.default_rng(7).integers(8, 17, nseg).astype(np.int64)
-    off = np.zeros(nseg + 1, np.int64)
-    np.cumsum(lens, out=off[1:])
-    assert sr.segmented_layout_flags(sms, sr.I32, nseg, lens.mean(), lens.std(), lens.max()) == sr.F_LANE_SEGMENTS
-    x = workloads.uniform_i32(int(off[-1]), seed=7)
-    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
-    ref = oracle.segsum_i32(x, off)
-    for s in (nat, None):
-        out.fill_(-1)
-        sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), nseg, sr.I32, out.data_ptr(),
-                                                      lens.mean(), lens.std(), lens.max()))
-        assert np.array_equal(out.cpu().numpy(), ref)
+    rng = np.random.default_rng(6)
+    for lens, form in ((rng.integers(1, 600, nseg), sr.F_WARP_SEGMENTS),    # spread lengths
+                       (rng.integers(8, 17, nseg), sr.F_LANE_SEGMENTS),     # tiny: 16-byte vectors
+                       (rng.integers(100, 201, nseg), sr.F_LANE_SEGMENTS)):  # 600 bytes: 32-byte vectors
+        lens = lens.astype(np.int64)
+        off = np.zeros(nseg + 1, np.int64)
+        np.cumsum(lens, out=off[1:])
+        assert sr.segmented_layout_flags(sms, sr.I32, nseg, lens.mean(), lens.std(), lens.max()) == form
+        x = workloads.uniform_i32(int(off[-1]), seed=int(lens[0]))
+        xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(off).cuda()
+        out = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+        ref = oracle.segsum_i32(x, off)
+        for s in (nat, None):
+            out.fill_(-1)
+            sr.check(sr.reduce_sum_segmented_selected_ptr(s, xd.data_ptr(), od.data_ptr(), nseg, sr.I32,
+                                                          out.data_ptr(), lens.mean(), lens.std(), lens.max()))
+            assert np.array_equal(out.cpu().numpy(), ref), form
+        del xd, od, out
     nat.close()

@@ -322,7 +322,8 @@ LANE = 0x8000  # SR_F_LANE_SEGMENTS: whole segments per thread, no grid stage
 
 @pytest.mark.parametrize("form,vec,unroll,block", [
     (WARP, 16, 4, 256), (WARP, 32, 1, 64), (WARP, 16, 8, 512), (WARP, 32, 2, 128), (WARP, 16, 1, 32),
-    (WARP, 32, 8, 256), (LANE, 16, 4, 256), (LANE, 16, 1, 32), (LANE, 32, 8, 512), (LANE, 16, 2, 128)])
+    (WARP, 32, 8, 256), (LANE, 16, 4, 256), (LANE, 16, 1, 32), (LANE, 32, 8, 512), (LANE, 16, 2, 128),
+    (LANE, 32, 4, 256), (LANE, 32, 1, 64)])
 def test_warp_segments(sr, form, vec, unroll, block):
     """The whole-segment forms (a warp, or a single thread, per segment):
     random layouts with empty, tiny and long segments (one of 100,000
