@@ -18,6 +18,8 @@
 //   grid.sync   : cooperative kernel, finishes after grid.sync();
 //   last-block  : per-segment ticket; the last contributing warp finishes;
 //   atomic      : spanning pieces atomically added into out (zeroed first).
+// The end of this file holds two forms without that split: whole segments
+// per warp and whole segments per thread (no carries, no grid stage).
 #pragma once
 
 #include <type_traits>
