@@ -217,7 +217,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=N_HEADLINE, help="elements (profiling runs use a smaller case)")
     ap.add_argument("--skip-extras", action="store_true", help="headline loop only (profiling runs)")
-    ap.add_argument("--suite", default=None, choices=["selector", "barrier", "precision", "sweep", "segmented", "shapes", "seglayouts"],
+    ap.add_argument("--suite", default=None, choices=["selector", "barrier", "precision", "sweep", "segmented", "shapes", "seglayouts",
+                             "latency"],
                     help="secondary measurement suites (JSON lines); the default run is the headline")
     ap.add_argument("--layout", default=None,
                     help="seglayouts suite: only the layouts whose name contains this text (profiling runs)")

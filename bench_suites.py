@@ -435,6 +435,62 @@ def seglayouts_suite(args):
     return 0
 
 
+def latency_suite(args):
+    """Small-n latency: device time per call of single-cluster shapes (no grid
+    stage; 1-16 CTAs of 128-512 threads, 16/32-byte vectors, unroll 1/2/4) in
+    CUDA graphs of 400 calls at n = 2^10..2^18 FP32, the five fastest per
+    size and SR_AUTO beside them; then a direct A/B of four cluster shapes
+    (graphs of 1000 calls, median of 5 alternating repetitions) at 2^14..2^18."""
+    import torch
+    import paper_2004_05371_gb300 as sr
+    import workloads
+    sr.load()
+    s = torch.cuda.Stream()
+    out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def per_call_us(x, n, cfg, calls, reps):
+        def body():
+            sr.check(sr.reduce_sum_ptr(x.data_ptr(), n, sr.F32, out.data_ptr(), cfg,
+                                       torch.cuda.current_stream().cuda_stream))
+        return _graph_time(torch, s, body, calls, reps=reps) * 1e3
+
+    for k in (10, 12, 14, 16, 18):
+        n = 1 << k
+        x = torch.from_numpy(workloads.uniform_f32(n, seed=0)).cuda()
+        timed = []
+        for lc in range(5):
+            for blk in (128, 256, 512):
+                for vec in (16, 32):
+                    for un in (1, 2, 4):
+                        cfg = sr.make_config(sr.SINGLE_CLUSTER | sr.CLUSTER(lc), block_threads=blk, vec_bytes=vec,
+                                             unroll=un)
+                        try:
+                            sr.plan(n, sr.F32, cfg)
+                            timed.append((per_call_us(x, n, cfg, 400, 5), 1 << lc, blk, vec, un))
+                        except sr.SRError:
+                            continue  # shape not launchable at this size
+        timed.sort()
+        for us, ctas, blk, vec, un in timed[:5]:
+            _emit({"suite": "latency", "log2n": k, "shape": "%d CTA x %d threads, %d B x %d" % (ctas, blk, vec, un),
+                   "us_per_call": round(us, 3)})
+        _emit({"suite": "latency", "log2n": k, "shape": "SR_AUTO",
+               "us_per_call": round(per_call_us(x, n, sr.make_config(sr.AUTO), 400, 5), 3)})
+    shapes = {"8 x 128": (3, 128), "16 x 256": (4, 256), "8 x 256": (3, 256), "16 x 128": (4, 128)}
+    for k in (14, 16, 17, 18):
+        n = 1 << k
+        x = torch.from_numpy(workloads.uniform_f32(n, seed=0)).cuda()
+        res = {name: [] for name in shapes}
+        for _ in range(5):
+            for name, (lc, blk) in shapes.items():
+                cfg = sr.make_config(sr.SINGLE_CLUSTER | sr.CLUSTER(lc), block_threads=blk, vec_bytes=32, unroll=2)
+                res[name].append(per_call_us(x, n, cfg, 1000, 5))
+        _emit({"suite": "latency_ab", "log2n": k,
+               **{name: round(sorted(v)[2], 3) for name, v in res.items()},
+               "spread": {name: round(max(v) - min(v), 3) for name, v in res.items()}})
+    return 0
+
+
 def run(name, args):
     return {"selector": selector_suite, "barrier": barrier_suite, "precision": precision_suite, "shapes": shapes_suite,
-            "sweep": sweep_suite, "segmented": segmented_suite, "seglayouts": seglayouts_suite}[name](args)
+            "sweep": sweep_suite, "segmented": segmented_suite, "seglayouts": seglayouts_suite,
+            "latency": latency_suite}[name](args)
