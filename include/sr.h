@@ -273,14 +273,16 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * explicit shape (vec_bytes, unroll, block_threads and stages all 0) calls
  * with 32768 or more segments take the TMA form, fewer the LDG one.
  * With SR_F_WARP_SEGMENTS whole segments go to single warps instead, with
- * SR_F_LANE_SEGMENTS to single threads (see the flags).
+ * SR_F_LANE_SEGMENTS to single threads (see the flags): no segment is split,
+ * the stage bits are ignored and the results are deterministic.
  * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE, SR_F_BULK,
- * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS, SR_F_LANE_SEGMENTS), block_threads (at most 512), ctas_per_sm, grid (at
- * most 65536 warps in total), vec_bytes, unroll, stages (TMA form), scale
- * (FP8).  SR_SINGLE_CLUSTER, cluster bits, and any two of SR_F_BULK,
+ * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS, SR_F_LANE_SEGMENTS),
+ * block_threads (at most 512), ctas_per_sm, grid (at most 65536 warps in
+ * total), vec_bytes, unroll, stages (TMA form), scale (FP8).
+ * SR_SINGLE_CLUSTER, cluster bits, and any two of SR_F_BULK,
  * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS and SR_F_LANE_SEGMENTS ->
- * SR_ERR_UNSUPPORTED; a ring larger than a CTA's
- * shared memory -> SR_ERR_LAUNCH.
+ * SR_ERR_UNSUPPORTED; a ring larger than a CTA's shared memory ->
+ * SR_ERR_LAUNCH.
  * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,
  * bad config), SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
 int sr_reduce_sum_segmented(const void* x, const int64_t* offsets, int64_t nseg, int dtype, void* out,
@@ -292,9 +294,9 @@ int sr_reduce_sum_segmented_ex(const void* x, const int64_t* offsets, int64_t ns
  * number of elements x holds (x may be NULL when n_elems == 0).  A small
  * kernel verifies offsets[0] >= 0, that every offset is >= its predecessor
  * and offsets[nseg] <= n_elems; if any fails, the summing kernels read
- * nothing (out is left as it was, or zero for SR_ATOMIC without
- * SR_F_WARP_SEGMENTS) and the next
- * sr_stream_status(stream) reports SR_ERR_ARG.  The plain entry points trust
+ * nothing (out is left as it was, or zero for SR_ATOMIC without a
+ * whole-segment form flag) and the next sr_stream_status(stream) reports
+ * SR_ERR_ARG.  The plain entry points trust
  * the caller with this contract; this one costs one extra kernel (8 bytes
  * read per segment).  The paper has no counterpart.  Host-side errors as
  * sr_reduce_sum_segmented_ex, plus SR_ERR_ARG for n_elems < 0 or x == NULL
