@@ -248,6 +248,120 @@ template <> __device__ __forceinline__ void acc_elem<kDtBF16, Pair>(Pair& a, con
 template <> __device__ __forceinline__ void acc_elem<kDtFP8, float>(float& a, const unsigned char* x, int64_t i) { acc_elem_fp8(a, x, i); }
 template <> __device__ __forceinline__ void acc_elem<kDtFP8, Pair>(Pair& a, const unsigned char* x, int64_t i) { acc_elem_fp8(a, x, i); }
 
+// ------------------------------------------------- thread-stage summation
+// Add one loaded vector (W 32-bit words) into the W word accumulators.
+template <int DT, class A, int W> struct AccVec {
+    __device__ static __forceinline__ void run(A (&a)[W], const uint32_t (&v)[W]) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc_word<DT>(a[w], v[w]);
+    }
+};
+// Plain FP8: every E4M3 value is an integer multiple of 2^-9 of magnitude at
+// most 448 (< 2^18 units of 2^-9), so up to 73 of them sum exactly in
+// binary32.  A vector's 16 or 32 values are therefore summed exactly and
+// added once, into word accumulator 0 (the others stay zero).
+template <int W> struct AccVec<kDtFP8, float, W> {
+    __device__ static __forceinline__ float word_sum(uint32_t w) {
+        __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+        __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+        float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&lo));
+        float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&hi));
+        return __fadd_rn(__fadd_rn(f0.x, f0.y), __fadd_rn(f1.x, f1.y));
+    }
+    __device__ static __forceinline__ float vec_sum(const uint32_t (&v)[W]) {
+        float t[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) t[w] = word_sum(v[w]);
+#pragma unroll
+        for (int s = W / 2; s >= 1; s >>= 1)
+#pragma unroll
+            for (int w = 0; w < s; ++w) t[w] = __fadd_rn(t[w], t[w + s]);
+        return t[0];
+    }
+    __device__ static __forceinline__ void run(float (&a)[W], const uint32_t (&v)[W]) {
+        a[0] = __fadd_rn(a[0], vec_sum(v));
+    }
+};
+
+// Dependent additions made into one word accumulator by one acc_word call.
+template <int DT> struct AddsPerWord { static constexpr int v = 1; };   // F32, I32; FP8 (a vector sums exactly first)
+template <> struct AddsPerWord<kDtBF16> { static constexpr int v = 2; };
+
+// The thread stage keeps W word accumulators (one per 32-bit lane of its
+// vector loads).  int64 sums are exact and compensated pairs carry their own
+// error term: for them Levels does nothing and the words are folded in order
+// at the end.  The plain binary32 form is blocked instead, so that no chain of
+// dependent additions grows with n (a chain of k same-sign additions can err
+// by ~k u |S|; on constant data 64 of them already exceed 4 eps32 |S|):
+//   - a word accumulator takes at most kBlockAdds additions; then (flush) the
+//     W words are folded pairwise into one block sum and restarted at zero;
+//   - block sums enter level 1; every 16 blocks level 1 is added into level 2,
+//     every 256 blocks level 2 into level 3.
+// Every chain is then at most ~16 additions long up to 2^16 blocks per thread
+// (2^20 values per word), and the thread's sum is ((fold + l1) + l2) + l3.
+constexpr int kBlockAdds = 16;  // Levels<float> counts blocks in the upper bits of c, adds in the low 4
+
+template <class A> struct Levels {
+    __device__ __forceinline__ void init() {}
+    template <int W> __device__ __forceinline__ void flush(A (&)[W]) {}
+    template <int ADDS, int W> __device__ __forceinline__ void after(A (&)[W]) {}
+    template <int W> __device__ __forceinline__ A total(const A (&a)[W]) const {
+        A t = a[0];
+#pragma unroll
+        for (int w = 1; w < W; ++w) t = Op<A>::add(t, a[w]);
+        return t;
+    }
+};
+
+template <> struct Levels<float> {
+    float l1, l2, l3;
+    uint32_t c;  // (blocks << 4) | additions made into the words in this block
+    __device__ __forceinline__ void init() {
+        l1 = l2 = l3 = 0.f;
+        c = 0u;
+    }
+    template <int W> __device__ __forceinline__ static float fold(float (&a)[W]) {
+#pragma unroll
+        for (int s = W / 2; s >= 1; s >>= 1)
+#pragma unroll
+            for (int w = 0; w < s; ++w) a[w] = __fadd_rn(a[w], a[w + s]);
+        return a[0];
+    }
+    // Block sum into level 1 (block count already advanced in c), carries.
+    template <int W> __device__ __forceinline__ void close(float (&a)[W]) {
+        l1 = __fadd_rn(l1, fold(a));
+#pragma unroll
+        for (int w = 0; w < W; ++w) a[w] = 0.f;
+        if ((c & 0xF0u) == 0u) {
+            l2 = __fadd_rn(l2, l1);
+            l1 = 0.f;
+            if ((c & 0xFF0u) == 0u) {
+                l3 = __fadd_rn(l3, l2);
+                l2 = 0.f;
+            }
+        }
+    }
+    // End of a block whose length the caller controls.
+    template <int W> __device__ __forceinline__ void flush(float (&a)[W]) {
+        c = (c | 15u) + 1u;
+        close(a);
+    }
+    // ADDS (a power of two <= kBlockAdds) additions were just made into each
+    // word: the block closes when the low four bits of c carry, i.e. when
+    // (c & 15) < ADDS after the addition.
+    template <int ADDS, int W> __device__ __forceinline__ void after(float (&a)[W]) {
+        static_assert(ADDS >= 1 && ADDS <= kBlockAdds && (ADDS & (ADDS - 1)) == 0, "block size");
+        c += (uint32_t)ADDS;
+        if ((c & 15u) < (uint32_t)ADDS) {
+            c &= ~15u;
+            close(a);
+        }
+    }
+    template <int W> __device__ __forceinline__ float total(float (&a)[W]) const {
+        return __fadd_rn(__fadd_rn(__fadd_rn(fold(a), l1), l2), l3);
+    }
+};
+
 // ------------------------------------------------------------ partials
 // A unit partial stored in the workspace: 16 bytes per slot.
 //   int32 input          -> int64

@@ -12,6 +12,8 @@
 //   5. grid   : two-kernel | atomic | last-block-done | grid.sync | none.
 #pragma once
 
+#include <type_traits>
+
 #include "sr_device.cuh"
 #include "sr_kparams.h"
 
@@ -64,10 +66,19 @@ template <class A> __device__ __forceinline__ void out_atomic(A v, const KParams
 // unit runs it) and write the result.  Whole block participates.
 template <class P> __device__ __forceinline__ void reduce_slots(const KParams& p) {
     __shared__ __align__(16) unsigned char scratch_raw[32 * sizeof(P)];
-    P v = Op<P>::zero();
-    for (int i = threadIdx.x; i < p.units; i += blockDim.x)
-        v = Op<P>::add(v, slot_load<P>(p.partials + (size_t)i * 16));
-    v = block_reduce(v, reinterpret_cast<P*>(scratch_raw));
+    // blocks of kBlockAdds slots per thread (binary32: no long same-sign chain)
+    P acc[1] = {Op<P>::zero()};
+    Levels<P> lv;
+    lv.init();
+    int n = 0;
+    for (int i = threadIdx.x; i < p.units; i += blockDim.x) {
+        acc[0] = Op<P>::add(acc[0], slot_load<P>(p.partials + (size_t)i * 16));
+        if (++n == kBlockAdds) {
+            lv.flush(acc);
+            n = 0;
+        }
+    }
+    P v = block_reduce(lv.total(acc), reinterpret_cast<P*>(scratch_raw));
     if (threadIdx.x == 0) out_write(v, p);
 }
 
@@ -210,33 +221,50 @@ __global__ void __launch_bounds__(1024) reduce_ldg_kernel(const KParams p) {
     A acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = Op<A>::zero();
+    Levels<A> lv;
+    lv.init();
 
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const unsigned char* body = p.x + p.head * ElemBytes<DT>::v;
 
     int64_t i = tid;
-    for (; i + (UNROLL - 1) * nth < p.nvec; i += UNROLL * nth) {
-        uint32_t v[UNROLL][W];
+    if constexpr (std::is_same<A, float>::value) {
+        // blocked (Levels<float>): the loop is unrolled by hand only; the
+        // compiler's own unrolling of the block bookkeeping costs registers
+#pragma unroll (UNROLL == 1 ? 2 : 1)
+        for (; i + (UNROLL - 1) * nth < p.nvec; i += UNROLL * nth) {
+            uint32_t v[UNROLL][W];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) ldg_vec(body + (i + u * nth) * VB, v[u]);
+            for (int u = 0; u < UNROLL; ++u) ldg_vec(body + (i + u * nth) * VB, v[u]);
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u)
+            for (int u = 0; u < UNROLL; ++u) AccVec<DT, A, W>::run(acc, v[u]);
+            lv.template after<UNROLL * AddsPerWord<DT>::v>(acc);
+        }
+        for (; i < p.nvec; i += nth) {
+            uint32_t v[W];
+            ldg_vec(body + i * VB, v);
+            AccVec<DT, A, W>::run(acc, v);
+            lv.template after<AddsPerWord<DT>::v>(acc);
+        }
+    } else {
+        for (; i + (UNROLL - 1) * nth < p.nvec; i += UNROLL * nth) {
+            uint32_t v[UNROLL][W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) acc_word<DT>(acc[w], v[u][w]);
-    }
-    for (; i < p.nvec; i += nth) {
-        uint32_t v[W];
-        ldg_vec(body + i * VB, v);
+            for (int u = 0; u < UNROLL; ++u) ldg_vec(body + (i + u * nth) * VB, v[u]);
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc_word<DT>(acc[w], v[w]);
+            for (int u = 0; u < UNROLL; ++u) AccVec<DT, A, W>::run(acc, v[u]);
+        }
+        for (; i < p.nvec; i += nth) {
+            uint32_t v[W];
+            ldg_vec(body + i * VB, v);
+            AccVec<DT, A, W>::run(acc, v);
+        }
     }
     if (tid < p.head) acc_elem<DT>(acc[0], p.x, tid);
     if (tid < p.ntail) acc_elem<DT>(acc[0], p.x, p.tail_begin + tid);
 
-    A t = acc[0];
-#pragma unroll
-    for (int w = 1; w < W; ++w) t = Op<A>::add(t, acc[w]);
+    A t = lv.total(acc);
     finish(t, p);
 }
 
@@ -275,6 +303,8 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
     A acc[4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) acc[w] = Op<A>::zero();
+    Levels<A> lv;
+    lv.init();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -307,6 +337,10 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
         }
     } else {
         const int ctid = threadIdx.x - 32, nct = ncw * 32;
+        const int tile_chunks = p.tile_bytes >> 4;
+        const int q_full = ctid < tile_chunks ? (tile_chunks - 1 - ctid) / nct + 1 : 0;
+        (void)q_full;
+        bool pending = false;  // float: acc holds a block to fold
         for (int64_t k = 0; k < my_tiles; ++k) {
             const int s = (int)(k % S);
             const uint32_t ph = (uint32_t)((k / S) & 1);
@@ -319,33 +353,75 @@ __global__ void __launch_bounds__(1024) reduce_bulk_kernel(const KParams p) {
             const int64_t t = (int64_t)blockIdx.x + k * gridDim.x;
             const int chunks = (int)(min((int64_t)p.tile_bytes, p.body_bytes - t * p.tile_bytes) >> 4);
             const uint32_t base = ring + (uint32_t)s * p.tile_bytes;
-            int j = ctid;
-            for (; j + nct < chunks; j += 2 * nct) {
-                uint32_t v0[4], v1[4];
-                lds_vec(base + 16u * j, v0);
-                lds_vec(base + 16u * (j + nct), v1);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) acc_word<DT>(acc[w], v0[w]);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) acc_word<DT>(acc[w], v1[w]);
-            }
-            for (; j < chunks; j += nct) {
-                uint32_t v0[4];
-                lds_vec(base + 16u * j, v0);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) acc_word<DT>(acc[w], v0[w]);
+            if constexpr (std::is_same<A, float>::value) {
+                // This thread's q chunks of the tile form one block (at most
+                // kChunks: kBlockAdds additions into each word), folded after
+                // the stage is released; more chunks than that per tile are
+                // split into blocks of kChunks.
+                constexpr int kChunks = kBlockAdds / AddsPerWord<DT>::v;
+                const int q = chunks == tile_chunks ? q_full
+                                                    : (ctid < chunks ? (chunks - 1 - ctid) / nct + 1 : 0);
+                if (q <= kChunks) {
+                    int j = ctid;
+                    for (; j + nct < chunks; j += 2 * nct) {
+                        uint32_t v0[4], v1[4];
+                        lds_vec(base + 16u * j, v0);
+                        lds_vec(base + 16u * (j + nct), v1);
+                        AccVec<DT, A, 4>::run(acc, v0);
+                        AccVec<DT, A, 4>::run(acc, v1);
+                    }
+                    if (j < chunks) {
+                        uint32_t v0[4];
+                        lds_vec(base + 16u * j, v0);
+                        AccVec<DT, A, 4>::run(acc, v0);
+                    }
+                } else {
+                    int j = ctid;
+                    for (int done = 0; done < q; done += kChunks) {
+                        if (done) lv.flush(acc);
+                        const int nb = q - done < kChunks ? q - done : kChunks;
+                        int c = 0;
+                        for (; c + 1 < nb; c += 2, j += 2 * nct) {
+                            uint32_t v0[4], v1[4];
+                            lds_vec(base + 16u * j, v0);
+                            lds_vec(base + 16u * (j + nct), v1);
+                            AccVec<DT, A, 4>::run(acc, v0);
+                            AccVec<DT, A, 4>::run(acc, v1);
+                        }
+                        if (c < nb) {
+                            uint32_t v0[4];
+                            lds_vec(base + 16u * j, v0);
+                            AccVec<DT, A, 4>::run(acc, v0);
+                            j += nct;
+                        }
+                    }
+                }
+                pending = q > 0;
+            } else {
+                int j = ctid;
+                for (; j + nct < chunks; j += 2 * nct) {
+                    uint32_t v0[4], v1[4];
+                    lds_vec(base + 16u * j, v0);
+                    lds_vec(base + 16u * (j + nct), v1);
+                    AccVec<DT, A, 4>::run(acc, v0);
+                    AccVec<DT, A, 4>::run(acc, v1);
+                }
+                for (; j < chunks; j += nct) {
+                    uint32_t v0[4];
+                    lds_vec(base + 16u * j, v0);
+                    AccVec<DT, A, 4>::run(acc, v0);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8u * s);
+            if (pending) lv.flush(acc);
         }
         const int64_t gct = (int64_t)blockIdx.x * nct + ctid;
         if (gct < p.head) acc_elem<DT>(acc[0], p.x, gct);
         if (gct < p.ntail) acc_elem<DT>(acc[0], p.x, p.tail_begin + gct);
     }
 
-    A t = acc[0];
-#pragma unroll
-    for (int w = 1; w < 4; ++w) t = Op<A>::add(t, acc[w]);
+    A t = lv.total(acc);
     finish(t, p);
 }
 

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 def test_plan_auto_regimes(sr):
     """SR_AUTO: one CTA up to 16 KiB, a 16-CTA cluster up to 1 MiB, the
     two-kernel form up to 512 MiB, then last-block-done on the TMA ring
-    (FP32 sizes)."""
+    (FP32 sizes; the ring's shape per dtype)."""
     cases = [(1 << 10, sr.SINGLE_CLUSTER, 0), (1 << 12, sr.SINGLE_CLUSTER, 0), (1 << 14, sr.SINGLE_CLUSTER, 4),
              (1 << 18, sr.SINGLE_CLUSTER, 4), (1 << 20, sr.TWO_KERNEL, 0), (1 << 24, sr.TWO_KERNEL, 0),
              (1 << 26, sr.TWO_KERNEL, 0), (1 << 27, sr.TWO_KERNEL, 0), (1 << 28, sr.LAST_BLOCK, 0)]
@@ -25,7 +25,13 @@ def test_plan_auto_regimes(sr):
     r = sr.plan(1 << 27, sr.F32)
     assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 1, 512) and not r.variant & sr.F_BULK
     r = sr.plan(1 << 28, sr.F32)
+    assert r.variant & sr.F_BULK and (r.tile_bytes, r.stages, r.block_threads) == (65536, 2, 288)
+    r = sr.plan(1 << 28, sr.I32)
     assert r.variant & sr.F_BULK and (r.tile_bytes, r.stages, r.block_threads) == (32768, 4, 160)
+    r = sr.plan(1 << 30, sr.FP8E4M3)
+    assert r.variant & sr.F_BULK and (r.tile_bytes, r.stages, r.block_threads) == (65536, 3, 288)
+    r = sr.plan(1 << 28, sr.FP8E4M3)
+    assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 4, 512) and not r.variant & sr.F_BULK
     r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.F_KAHAN))
     assert r.variant & sr.F_BULK and r.tile_bytes == 32768 and r.stages == 4
     # explicit fields override the table; a vector width or unroll selects the LDG path
