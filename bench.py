@@ -385,42 +385,88 @@ def main():
     return 0
 
 
-def latency_small(sr, torch, dev, stream):
-    """Device time per call at n=2^14 (AUTO choice), averaged over a CUDA graph
-    of 200 back-to-back calls, plus the host round trip of a single call."""
+def latency_small(sr, torch, dev, stream, calls=1000):
+    """Device time per call at n = 2^14 FP32 (SR_AUTO's choice) in a CUDA
+    graph of `calls` back-to-back calls: warm (the same 64 KiB input every
+    call, L2-resident), cold (each call after a 256 MiB write that evicts it
+    from L2; the graph of the writes alone is timed and subtracted), CUB's
+    DeviceReduce::Sum warm in the same protocol, and the host round trip of
+    one call (launch, then stream synchronize)."""
+    import libcmp
     import workloads
     x = torch.from_numpy(workloads.uniform_f32(N_LATENCY, seed=0)).to(dev)
     out = torch.empty((), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     cfg = sr.make_config(sr.AUTO)
     s = torch.cuda.Stream(dev)
-    with torch.cuda.stream(s):
-        for _ in range(5):
-            sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg, s.cuda_stream))
-    s.synchronize()
-    g = torch.cuda.CUDAGraph()
-    calls = 200
-    with torch.cuda.graph(g, stream=s):
-        for _ in range(calls):
-            sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg,
-                                       torch.cuda.current_stream().cuda_stream))
-    g.replay()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    a.record(stream)
-    for _ in range(reps):
+
+    def graph_us(body, n_calls, reps=5):
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                body()      # the stream's first call allocates its workspace: before capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(n_calls):
+                body()
         g.replay()
-    b.record(stream)
-    torch.cuda.synchronize()
-    graph_us = a.elapsed_time(b) * 1e3 / (reps * calls)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / (reps * n_calls)
+
+    def ours():
+        sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg,
+                                   torch.cuda.current_stream().cuda_stream))
+    warm = graph_us(ours, calls)
+    cold_calls = 100
+    flush_only = graph_us(lambda: flush.fill_(1), cold_calls)
+    cold = graph_us(lambda: (flush.fill_(1), ours()), cold_calls) - flush_only
+    cub = None
+    try:
+        libcmp.build()
+        cmp = libcmp.lib()
+        libcmp.check(cmp.cmp_prepare(N_LATENCY), "cmp_prepare")
+        cub = graph_us(lambda: libcmp.check(cmp.cmp_cub_sum_f32(x.data_ptr(), N_LATENCY, out.data_ptr(),
+                                                                torch.cuda.current_stream().cuda_stream), "cub"),
+                       calls)
+    except Exception:
+        cub = None
     rt = []
     for _ in range(50):
         t0 = time.perf_counter()
         sr.check(sr.reduce_sum_ptr(x.data_ptr(), N_LATENCY, sr.F32, out.data_ptr(), cfg, stream.cuda_stream))
         stream.synchronize()
         rt.append((time.perf_counter() - t0) * 1e6)
-    return {"graph_us_per_call": round(graph_us, 3), "host_roundtrip_us_median": round(statistics.median(rt), 2),
+    return {"graph_us_per_call": round(warm, 3), "calls": calls, "cold_us": round(cold, 3),
+            "cold_protocol": "graph of %d (256 MiB write, call) pairs minus a graph of the writes alone" % cold_calls,
+            "cub_us": None if cub is None else round(cub, 3),
+            "host_roundtrip_us_median": round(statistics.median(rt), 2),
             "variant": "0x%x" % sr.plan(N_LATENCY, sr.F32, cfg).variant}
+
+
+def segment_sums_f64(x, off):
+    """Per-segment binary64 sums of x and of |x| for a CSR layout covering
+    all of x (numpy; the accuracy figures of the segmented legs; the oracle
+    stays out of the GPU arm).  Empty segments sum to 0."""
+    import numpy as np
+    assert int(off[-1]) == x.size
+    lens = np.diff(off)
+    nz = lens > 0
+    starts = off[:-1][nz].astype(np.int64)
+    x64 = x.astype(np.float64)
+    s = np.zeros(lens.size)
+    a = np.zeros(lens.size)
+    if starts.size:
+        # reduceat sums x[starts[k]:starts[k+1]] and x[starts[-1]:]: with the
+        # empty segments left out these are exactly the non-empty segments
+        s[nz] = np.add.reduceat(x64, starts)
+        a[nz] = np.add.reduceat(np.abs(x64), starts)
+    return s, a
 
 
 def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
@@ -429,7 +475,6 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
     launch, against one plain sr_reduce_sum launch per segment (the plain
     launches timed both as a captured graph of 10,000 launches and eagerly)."""
     import numpy as np
-    import oracle
     import workloads
     off = workloads.segment_offsets(nseg, 1 << 28, seed=0)
     n = int(off[-1])
@@ -490,12 +535,15 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
                                        cs.cuda_stream))
     plain_graph_ms = time_it(lambda: pg_graph.replay(), 3)
     torch.cuda.synchronize()
-    ref = oracle.segsum_f32(x_np, off)
-    sabs = oracle.segsum_abs_f32(x_np, off)
+    ref, sabs = segment_sums_f64(x_np, off)
     gate = 4 * 2.0 ** -23 * sabs
     err_b = float(np.max(np.abs(out_b.cpu().numpy() - ref) / gate))
     err_p = float(np.max(np.abs(out_p.cpu().numpy() - ref) / gate))
     g.close()
+    try:
+        selected = learned_selected(sr, torch, stream, x, od, off, nseg, ref, gate, plain_graph_ms, batched_ms)
+    except Exception as e:  # reported, never hides the rest
+        selected = {"error": str(e)[:300]}
     r = sr.plan_segmented(nseg, sr.F32, cfg)
     return {"n": n, "nseg": nseg, "batched_us": round(batched_ms * 1e3, 2),
             "batched_gbs": round(n * 4 / (batched_ms * 1e-3) / 1e9, 1),
@@ -503,10 +551,73 @@ def batched_vs_plain(sr, torch, dev, stream, nseg=10_000):
             "speedup_vs_plain_graph": round(plain_graph_ms / batched_ms, 2),
             "speedup_vs_plain_eager": round(eager_ms / batched_ms, 2),
             "max_err_over_gate_batched": round(err_b, 4), "max_err_over_gate_plain": round(err_p, 4),
+            "learned_selected": selected,
             "batched_config": {"stage": sr.STAGE_NAMES.get(r.variant & sr.STAGE_MASK), "grid": r.grid,
                                "block": r.block_threads, "vec_bytes": r.vec_bytes, "unroll": r.unroll,
                                "chosen_by": "sr_autotune over %d candidates (%.0f us best, %.0f us default)"
                                             % (len(cands), us[best], default_us)}}
+
+
+def learned_selected(sr, torch, stream, x, od, off, nseg, ref, gate, plain_graph_ms, batched_ms,
+                     train_shapes=320):
+    """The learned-selected form of the same segmented workload
+    (sr_reduce_sum_segmented_selected): a selector trained in this run on
+    exhaustive autotuner timings of random shapes (n <= 2^28), its choice for
+    this workload, the first call's host cost (features, inference kernel,
+    class read back, launch) and the device time of later calls (choice
+    memoised), against the plain per-segment launches and the autotuned
+    batched launch."""
+    import numpy as np
+    from paper_2004_05371_gb300 import selector
+    import workloads
+    sms = torch.cuda.get_device_properties(x.device).multi_processor_count
+    cands = sr.candidates(sms)
+    t0 = time.perf_counter()
+    tr = workloads.selector_shapes(train_shapes, seed=101)
+    for s in tr:
+        s["n"] = min(s["n"], 1 << 28)
+        s["nseg"] = min(s["nseg"], s["n"])
+    off_tr = [workloads.shape_offsets(s, i) if s["nseg"] > 1 else None for i, s in enumerate(tr)]
+    T = selector.collect_timings(tr, off_tr, cands)
+    t_collect = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    sel, _ = selector.train(selector.features(tr, off_tr), selector.soft_targets(T), steps=3000)
+    t_train = time.perf_counter() - t1
+    nat = sel.native(cands)
+    lens = np.diff(off).astype(np.float64)
+    out = torch.empty(nseg, dtype=torch.float32, device=x.device)
+    sh = stream.cuda_stream
+
+    def call():
+        sr.check(sr.reduce_sum_segmented_selected_ptr(nat, x.data_ptr(), od.data_ptr(), nseg, sr.F32, out.data_ptr(),
+                                                      lens.mean(), lens.std(), lens.max(), stream=sh))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    call()
+    stream.synchronize()
+    first_us = (time.perf_counter() - t2) * 1e6
+    for _ in range(3):
+        call()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(20):
+        call()
+    b.record(stream)
+    torch.cuda.synchronize()
+    sel_ms = a.elapsed_time(b) / 20
+    err = float(np.max(np.abs(out.cpu().numpy() - ref) / gate))
+    c = nat.choose(int(round(lens.mean() * nseg)), sr.F32, nseg, lens.mean(), lens.std(), lens.max())
+    nat.close()
+    return {"selected_us": round(sel_ms * 1e3, 2), "first_call_us": round(first_us, 1),
+            "speedup_vs_plain_graph": round(plain_graph_ms / sel_ms, 2),
+            "vs_autotuned_batched": round(sel_ms / batched_ms - 1.0, 4),
+            "max_err_over_gate": round(err, 4),
+            "choice": {"stage": sr.STAGE_NAMES.get(c.variant & sr.STAGE_MASK), "grid": c.grid,
+                       "vec_bytes": c.vec_bytes},
+            "selector": "MLP 9-64-64-40 trained in this run: %d shapes x %d candidates timed by sr_autotune "
+                        "(%.1f s), 3000 Adam steps by the library's kernels (%.1f s)"
+                        % (len(tr), len(cands), t_collect, t_train)}
 
 
 def cub_reference(torch, x, n, stream, args):
@@ -574,10 +685,36 @@ def end_to_end(sr, torch, dev, stream, x_host, args):
                                                                     dcfg, sh)))
         direct = {"gbs": round(n * 4 / ddt / 1e9, 2), "ms_per_step": round(ddt * 1e3, 3),
                   "path": "sr_reduce_sum_host with SR_F_HOST_DIRECT (kernel reads pinned host memory in place)"}
+    raw = raw_h2d_bound(torch, dev, pinned, timed_blocks)
     return {"value": round(n * 4 / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": n * 4,
+            "raw_h2d_gbs": raw, "value_over_raw_h2d": round((n * 4 / dt / 1e9) / max(raw.values()), 4),
             "d2h_bytes_per_step": 4, "ms_per_step": round(dt * 1e3, 3), "result": float(res.item()),
             "path": "sr_reduce_sum_host: pinned host input, 64 MiB chunks on two copy streams overlapped "
                     "with the chunk reductions, final combine, 4-byte read-back", "direct_read": direct}
+
+
+def raw_h2d_bound(torch, dev, pinned, timed_blocks):
+    """The host link's own figure for the same bytes: the pinned 1 GiB input
+    copied to the device with no reduction, as one cudaMemcpyAsync and split
+    into 2 and 4 chunks on as many streams (one cudaMemcpyAsync per chunk),
+    host wall clock around copy + synchronize, as the e2e steps are timed."""
+    nbytes = pinned.numel() * pinned.element_size()
+    dst = torch.empty(pinned.numel(), dtype=pinned.dtype, device=dev)
+    res = {}
+    for k in (1, 2, 4):
+        streams = [torch.cuda.Stream(dev) for _ in range(k)]
+        step = (pinned.numel() + k - 1) // k
+
+        def copy():
+            for i, st in enumerate(streams):
+                with torch.cuda.stream(st):
+                    dst[i * step:(i + 1) * step].copy_(pinned[i * step:(i + 1) * step], non_blocking=True)
+            for st in streams:
+                st.synchronize()
+        copy()
+        res["streams_%d" % k] = round(nbytes / timed_blocks(copy) / 1e9, 2)
+    del dst
+    return res
 
 
 if __name__ == "__main__":

@@ -66,11 +66,20 @@ def selector_suite(args):
     fixed = [i for i, c in enumerate(cands) if c.variant == sr.LAST_BLOCK and c.grid == 8 * sms and
              c.vec_bytes == 16][0]
     r_fixed = selector.regret(Tte, np.full(len(te), fixed))
-    # inference cost of one shape (the kernel, device time)
+    # inference cost of one shape: device time per call of the predict kernel
+    # in a CUDA graph of 200 calls, and per eager call (host launch included)
     x1 = torch.from_numpy(((Xte[:1] - sel.mu) / sel.sd).astype(np.float32)).cuda()
     cls = torch.empty(1, dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream()
-    infer_us = _time_calls(torch, lambda: sel.mlp.predict(x1, cls), 200, st) * 1e3
+    infer_us = _graph_time(torch, torch.cuda.Stream(), lambda: sel.mlp.predict(x1, cls), 200) * 1e3
+    infer_eager_us = _time_calls(torch, lambda: sel.mlp.predict(x1, cls), 200, st) * 1e3
+    # one whole per-call choice (features, predict, class read back) for a shape not seen before
+    nat = sel.native(cands)
+    t0 = time.perf_counter()
+    for i in range(50):
+        nat.choose((1 << 20) + 4096 * i, sr.F32)
+    choose_us = (time.perf_counter() - t0) / 50 * 1e6
+    nat.close()
 
     def summ(r):
         return {"mean": round(float(r.mean()), 4), "median": round(float(np.median(r)), 4),
@@ -82,7 +91,8 @@ def selector_suite(args):
            "regret_model": summ(r_model), "regret_model_fitted": summ(r_fit),
            "model_fitted_params": {f: round(getattr(fitted, f), 3) for f in selector.FIT_FIELDS},
            "regret_fixed_default": summ(r_fixed),
-           "mlp_inference_us_per_call": round(infer_us, 2)})
+           "mlp_inference_us_per_call": round(infer_us, 2), "mlp_inference_eager_us_per_call": round(infer_eager_us, 2),
+           "first_choice_us_per_shape": round(choose_us, 2)})
     return 0
 
 

@@ -532,7 +532,12 @@ int sr_reduce_sum_segmented_selected(sr_selector selector, const void* x, const 
  *    call resets the ticket on `stream` before its kernel.  Calls whose work
  *    overlaps on the GPU (different streams, no ordering between them) race on
  *    the array and give wrong results: order them on one stream.
- * Errors: as sr_reduce_sum_ex. */
+ * Errors: the host-side statuses of sr_reduce_sum_ex (argument, dtype, launch
+ * and CUDA errors), returned by the call.  There are no device-side errors to
+ * report: the kernel it runs (vector loads, last-block-done finish) has no
+ * bounded wait and sets no error word, which is why SR_F_BULK (whose copy
+ * ring waits on mbarriers) is refused here; sr_stream_status reports nothing
+ * about these calls. */
 int sr_reduce_sum_noalloc(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg,
                           sr_stream_t stream);
 

@@ -6,7 +6,9 @@
 //                       CTA's partial gradient is written to its own slot;
 //   mlp_update_kernel : sums the CTA partials in a fixed order (deterministic)
 //                       and applies one Adam step;
-//   mlp_predict_kernel: forward pass and argmax (the inference kernel).
+//   mlp_predict_kernel: forward pass and argmax (the inference kernel): one
+//                       CTA per sample, weights held in registers, each
+//                       layer's dot products split over all 256 threads.
 // Parameter layout (row-major, one contiguous float array):
 //   W1[in][h], b1[h], W2[h][h], b2[h], W3[h][out], b3[out].
 #include <cmath>
@@ -180,29 +182,80 @@ __global__ void mlp_update_kernel(int64_t P, int nparts, const float* __restrict
     }
 }
 
+// Inference: one CTA per sample (grid-stride over the batch), 256 threads.
+// Each layer's dot products are split four ways: thread (part, col) sums
+// rows [part*k, part*k + k) of column col, the four partials meet in shared
+// memory and are added in part order (deterministic).  Every thread loads its
+// slices of W1, W2 and W3 into registers before anything waits, so the weights
+// cost one trip to L2, not one per layer; the 7,400 parameters are never
+// staged through shared memory.
+constexpr int kParts = 4;
+constexpr int kR1 = kMaxIn / kParts, kR2 = kMaxH / kParts;  // rows per part (maximum)
+
 __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(MlpDims d, const float* __restrict__ params,
                                                                const float* __restrict__ X, int B,
                                                                int* __restrict__ cls, float* __restrict__ logits) {
-    extern __shared__ float sm[];
-    float* w = sm;
-    float* x = w + d.P;
-    float* h1 = x + kMaxIn;
-    float* h2 = h1 + kMaxH;
-    float* z = h2 + kMaxH;
-    const int t = threadIdx.x;
-    for (int64_t i = t; i < d.P; i += blockDim.x) w[i] = params[i];
-    __syncthreads();
-    const int b0 = blockIdx.x * kSamplesPerCta;
-    const int b1 = min(B, b0 + kSamplesPerCta);
-    for (int b = b0; b < b1; ++b) {
-        if (t < d.in) x[t] = X[(int64_t)b * d.in + t];
+    __shared__ float xs[kMaxIn], h1[kMaxH], h2[kMaxH], z[kMaxOut];
+    __shared__ float red[kParts][kMaxH];
+    const int tid = threadIdx.x, col = tid & (kMaxH - 1), part = tid / kMaxH;
+    const int k1 = (d.in + kParts - 1) / kParts, k2 = (d.h + kParts - 1) / kParts;
+    float w1[kR1], w2[kR2], w3[kR2];
+#pragma unroll
+    for (int r = 0; r < kR1; ++r) {
+        const int j = part * k1 + r;
+        w1[r] = (r < k1 && j < d.in && col < d.h) ? __ldg(params + d.oW1 + (int64_t)j * d.h + col) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < kR2; ++r) {
+        const int j = part * k2 + r;
+        const bool row = r < k2 && j < d.h;
+        w2[r] = (row && col < d.h) ? __ldg(params + d.oW2 + (int64_t)j * d.h + col) : 0.f;
+        w3[r] = (row && col < d.out) ? __ldg(params + d.oW3 + (int64_t)j * d.out + col) : 0.f;
+    }
+    const float bias1 = (part == 0 && col < d.h) ? __ldg(params + d.ob1 + col) : 0.f;
+    const float bias2 = (part == 0 && col < d.h) ? __ldg(params + d.ob2 + col) : 0.f;
+    const float bias3 = (part == 0 && col < d.out) ? __ldg(params + d.ob3 + col) : 0.f;
+
+    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+        if (tid < d.in) xs[tid] = X[(int64_t)b * d.in + tid];
         __syncthreads();
-        forward_one(d, w, x, h1, h2, z);
-        if (logits && t < d.out) logits[(int64_t)b * d.out + t] = z[t];
-        if (t < 32) {  // argmax, lowest index on ties
+        float a = 0.f;
+#pragma unroll
+        for (int r = 0; r < kR1; ++r)
+            if (r < k1 && part * k1 + r < d.in) a = fmaf(xs[part * k1 + r], w1[r], a);
+        red[part][col] = a;
+        __syncthreads();
+        if (tid < d.h) {
+            const float v = ((bias1 + red[0][tid]) + red[1][tid]) + (red[2][tid] + red[3][tid]);
+            h1[tid] = v > 0.f ? v : 0.f;
+        }
+        __syncthreads();
+        a = 0.f;
+#pragma unroll
+        for (int r = 0; r < kR2; ++r)
+            if (r < k2 && part * k2 + r < d.h) a = fmaf(h1[part * k2 + r], w2[r], a);
+        red[part][col] = a;
+        __syncthreads();
+        if (tid < d.h) {
+            const float v = ((bias2 + red[0][tid]) + red[1][tid]) + (red[2][tid] + red[3][tid]);
+            h2[tid] = v > 0.f ? v : 0.f;
+        }
+        __syncthreads();
+        a = 0.f;
+#pragma unroll
+        for (int r = 0; r < kR2; ++r)
+            if (r < k2 && part * k2 + r < d.h) a = fmaf(h2[part * k2 + r], w3[r], a);
+        red[part][col] = a;
+        __syncthreads();
+        if (tid < d.out) {
+            z[tid] = ((bias3 + red[0][tid]) + red[1][tid]) + (red[2][tid] + red[3][tid]);
+            if (logits) logits[(int64_t)b * d.out + tid] = z[tid];
+        }
+        __syncthreads();
+        if (tid < 32) {  // argmax, lowest index on ties
             float best = -INFINITY;
             int bi = d.out;
-            for (int o = t; o < d.out; o += 32)
+            for (int o = tid; o < d.out; o += 32)
                 if (z[o] > best) {
                     best = z[o];
                     bi = o;
@@ -215,9 +268,10 @@ __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(MlpDims d, const 
                     bi = oi;
                 }
             }
-            if (t == 0) cls[b] = bi;
+            if (tid == 0) cls[b] = bi;
         }
-        __syncthreads();
+        // the next sample's xs write is behind the barrier after it; z and
+        // red are rewritten only behind later barriers
     }
 }
 
@@ -334,11 +388,8 @@ int sr_mlp_train_step(sr_mlp h, const float* X, const float* Q, int batch, float
 
 int sr_mlp_predict(sr_mlp h, const float* X, int batch, int* cls, float* logits, sr_stream_t stream) {
     if (!h || !X || !cls || batch < 1) return SR_ERR_ARG;
-    const size_t smem = sizeof(float) * (size_t)(h->d.P + kMaxIn + 2 * kMaxH + kMaxOut);
-    int st = prepare_function((const void*)mlp_predict_kernel, smem, false);
-    if (st != SR_OK) return st;
-    const int blocks = (batch + kSamplesPerCta - 1) / kSamplesPerCta;
-    mlp_predict_kernel<<<blocks, kThreads, smem, (cudaStream_t)stream>>>(h->d, h->params, X, batch, cls, logits);
+    const int blocks = batch < 4096 ? batch : 4096;  // one CTA per sample, grid-stride beyond
+    mlp_predict_kernel<<<blocks, kThreads, 0, (cudaStream_t)stream>>>(h->d, h->params, X, batch, cls, logits);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SR_OK : status_from_cuda(e);
 }

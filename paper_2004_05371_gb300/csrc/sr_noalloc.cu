@@ -77,6 +77,9 @@ extern "C" int sr_reduce_sum_noalloc(const void* x, int64_t n, int dtype, void* 
     Workspace ws;
     ws.base = base;
     ws.tickets = reinterpret_cast<unsigned int*>(base);
+    // The load path here has no bounded wait and the finish is last-block-done
+    // (never grid.sync), so no kernel of this call writes the error word; it
+    // points into the array only so that the kernel parameters stay valid.
     ws.err = reinterpret_cast<int*>(base + 128);
     ws.partials = base + kNoAllocHeader;
     ws.seg = nullptr;

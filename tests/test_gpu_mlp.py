@@ -93,29 +93,57 @@ def test_training_learns_a_separable_task(sr):
 
 @pytest.mark.slow
 def test_learned_selector_beats_the_model_without_it(sr):
-    """Train on autotuner timings of random shapes, evaluate on held-out
-    shapes: the MLP's mean regret against exhaustive autotuning is reported
-    next to the performance-model selector's; the MLP must do better."""
+    """Train on autotuner timings of 480 random shapes, evaluate on 240
+    held-out shapes: the MLP's mean regret against exhaustive autotuning is at
+    most 5 % (the target) and below the performance-model selector's (the
+    method without it), hand-set or calibrated on the same training timings.
+    Sizes are capped at 2^26 elements to keep the test to about a minute."""
     from paper_2004_05371_gb300 import selector
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     cands = sr.candidates(sms)
-    tr = workloads.selector_shapes(160, seed=11)
-    te = workloads.selector_shapes(120, seed=12)
-    for s in tr + te:                     # keep the test quick: n <= 2^26
+    tr = workloads.selector_shapes(480, seed=11)
+    te = workloads.selector_shapes(240, seed=12)
+    for s in tr + te:
         s["n"] = min(s["n"], 1 << 26)
         s["nseg"] = min(s["nseg"], s["n"])
     off_tr = [workloads.shape_offsets(s, i) if s["nseg"] > 1 else None for i, s in enumerate(tr)]
     off_te = [workloads.shape_offsets(s, 10_000 + i) if s["nseg"] > 1 else None for i, s in enumerate(te)]
     Ttr = selector.collect_timings(tr, off_tr, cands)
     Tte = selector.collect_timings(te, off_te, cands)
-    sel, _ = selector.train(selector.features(tr, off_tr), selector.soft_targets(Ttr), steps=1500)
+    sel, _ = selector.train(selector.features(tr, off_tr), selector.soft_targets(Ttr), steps=3000)
     r_mlp = selector.regret(Tte, sel.choose(selector.features(te, off_te)))
     r_model = selector.regret(Tte, selector.analytic_choices(te, cands, selector.default_model_params(sms)))
     fitted, _ = selector.fit_model_params(tr, Ttr, cands, sms)
     r_fit = selector.regret(Tte, selector.analytic_choices(te, cands, fitted))
-    print("mean regret: mlp %.4f  model %.4f  model fitted %.4f" % (r_mlp.mean(), r_model.mean(), r_fit.mean()))
+    print("mean regret over %d held-out shapes: mlp %.4f  model %.4f  model fitted %.4f"
+          % (len(te), r_mlp.mean(), r_model.mean(), r_fit.mean()))
     assert np.all(np.isfinite(r_mlp)) and np.all(np.isfinite(r_model)) and np.all(np.isfinite(r_fit))
+    assert r_mlp.mean() <= 0.05, r_mlp.mean()
     assert r_mlp.mean() < min(r_model.mean(), r_fit.mean())
+
+
+def test_predict_kernel_batch_shapes(sr):
+    """The inference kernel on batches of 1 to 5,000 samples (one CTA per
+    sample up to 4,096, grid-stride beyond) and on narrower networks (input
+    and output widths not multiples of the four-way split): logits against
+    the FP64 oracle, classes where the top two logits are apart."""
+    for dims, B in (((9, 64, 40), 1), ((9, 64, 40), 4100), ((5, 24, 7), 33), ((32, 64, 64), 3), ((1, 1, 2), 5)):
+        rng = np.random.default_rng(B)
+        P = omlp.param_count(dims)
+        p = rng.normal(0, 0.3, P).astype(np.float32)
+        X = rng.normal(0, 1, (B, dims[0])).astype(np.float32)
+        m = sr.MLP(*dims)
+        m.set_params(p)
+        cls = torch.empty(B, dtype=torch.int32, device="cuda")
+        logits = torch.empty(B, dims[2], dtype=torch.float32, device="cuda")
+        m.predict(torch.from_numpy(X).cuda(), cls, logits)
+        torch.cuda.synchronize()
+        _, _, z = omlp.forward(p, X, dims)
+        assert np.max(np.abs(logits.cpu().numpy() - z)) <= 1e-4 * max(1.0, np.max(np.abs(z))), dims
+        top2 = np.sort(z, axis=1)[:, -2:]
+        clear = (top2[:, 1] - top2[:, 0]) > 1e-3
+        assert np.array_equal(cls.cpu().numpy()[clear], np.argmax(z, axis=1)[clear]), dims
+        m.close()
 
 
 def test_selected_entry_points(sr):

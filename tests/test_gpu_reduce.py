@@ -306,6 +306,40 @@ def test_max_size_2p30_int32_worst_case(sr):
 
 
 @pytest.mark.slow
+def test_full_size_2p30_f32(sr):
+    """The largest size of the sweep in binary32: 2^30 U[-1,1] values (4 GiB)
+    through SR_AUTO (the TMA ring), the ring explicitly and the two-kernel
+    form, against the exact sum."""
+    n = 1 << 30
+    x = workloads.uniform_f32(n, seed=30)
+    exact = oracle.exact_f32(x)
+    d = _to_dev(x, 0)
+    for st in (sr.AUTO, sr.LAST_BLOCK | sr.F_BULK, sr.TWO_KERNEL):
+        _check_f32(sr, x, float(sr.reduce_sum(d, variant=st).item()), st, exact)
+    del d, x
+    torch.cuda.empty_cache()
+    assert sr.stream_status() == sr.OK
+
+
+@pytest.mark.slow
+def test_cluster_forms_2p26(sr):
+    """Clusters of 4 CTAs (DSMEM merge) at 2^26 elements, above the sizes of
+    the per-shape sweep: last-block-done and two-kernel finishes, LDG and the
+    TMA ring, FP32 within the gates and int32 exactly."""
+    n = (1 << 26) + 7
+    xf = workloads.uniform_f32(n, seed=26)
+    xi = workloads.uniform_i32(n, seed=26)
+    exact_f, ref_i = oracle.exact_f32(xf), oracle.sum_i32(xi)
+    df, di = _to_dev(xf, 1), _to_dev(xi, 1)
+    for st in (sr.LAST_BLOCK, sr.TWO_KERNEL):
+        for flags in (0, sr.F_BULK):
+            v = st | sr.CLUSTER(2) | flags
+            _check_f32(sr, xf, float(sr.reduce_sum(df, variant=v).item()), v, exact_f)
+            assert int(sr.reduce_sum(di, variant=v).item()) == ref_i, hex(v)
+    assert sr.stream_status() == sr.OK
+
+
+@pytest.mark.slow
 def test_auto_regime_boundaries(sr):
     """SR_AUTO on both sides of each of its size thresholds (16 KiB one CTA,
     1 MiB one cluster, 64 MiB two-kernel with 32-byte loads, 512 MiB two-kernel

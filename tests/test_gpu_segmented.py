@@ -133,7 +133,7 @@ def test_bf16_and_fp8_segments(sr):
         ex = oracle.segexact_f32(dec_b, off)
         assert np.all(np.abs(got - ex) <= 4 * EPS32 * oracle.segsum_abs_f32(dec_b, off) + 1e-30)
         got = sr.reduce_sum_segmented(xd_f, od, config=sr.make_config(st, scale=deq)).cpu().numpy()
-        for s in range(0, 700, 37):
+        for s in range(700):  # every segment against its exact sum
             a, b = off[s], off[s + 1]
             exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
             sabs = float(np.abs(dec_f[a:b]).astype(np.float64).sum())

@@ -20,6 +20,10 @@ def test_noalloc_rejects_without_touching_the_gpu(sr):
     assert call(variant=sr.LAST_BLOCK, grid=4097) == sr.ERR_ARG          # above the 4096-unit maximum
     assert call(variant=sr.LAST_BLOCK | sr.CLUSTER(1), grid=8194) == sr.ERR_ARG
     assert sr.reduce_sum_noalloc_ptr(ALIGNED, -1, sr.F32, ALIGNED, None, stream=0) == sr.ERR_ARG
+    # the TMA ring waits on mbarriers and could report a timeout, which this
+    # entry point has no error word for: refused in every spelling
+    assert call(variant=sr.AUTO | sr.F_BULK) == sr.ERR_UNSUPPORTED
+    assert call(variant=sr.LAST_BLOCK | sr.F_BULK | sr.F_KAHAN) == sr.ERR_UNSUPPORTED
 
 
 @pytest.mark.gpu
@@ -46,3 +50,43 @@ def test_noalloc_matches_allocating_entry_point(sr):
                 bound = oracle.stated_fp32_bound(oracle.sum_abs_f32(x_np))
                 assert abs(float(out.item()) - float(ref.item())) <= bound
                 assert abs(float(out.item()) - oracle.to_float(oracle.exact_f32(x_np))) <= bound
+
+
+@pytest.mark.gpu
+def test_noalloc_flags_clusters_and_largest_grid(sr):
+    """The options the header says are honoured, each on two calls in a row
+    against sr_reduce_sum_ex with the same configuration: a cluster size, the
+    compensated path, the binary64 combine (8-byte output), and an explicit
+    grid of exactly the 4096-unit maximum; binary32 results within the
+    stated gate of the exact sum, int32 exactly."""
+    import torch
+    n = (1 << 22) + 5
+    xf = workloads.uniform_f32(n, seed=31)
+    xi = workloads.uniform_i32(n, seed=32)
+    exact = oracle.to_float(oracle.exact_f32(xf))
+    bound = oracle.stated_fp32_bound(oracle.sum_abs_f32(xf))
+    dfx, dix = torch.from_numpy(xf).cuda(), torch.from_numpy(xi).cuda()
+    cases = [(sr.LAST_BLOCK | sr.CLUSTER(1), {}, torch.float32),
+             (sr.LAST_BLOCK | sr.CLUSTER(3), {}, torch.float32),
+             (sr.LAST_BLOCK | sr.F_KAHAN, {}, torch.float32),
+             (sr.LAST_BLOCK | sr.F_KAHAN | sr.F_FP64_COMBINE, {}, torch.float64),
+             (sr.LAST_BLOCK | sr.F_FP64_COMBINE, {}, torch.float64),
+             (sr.LAST_BLOCK, {"grid": 4096, "block_threads": 256}, torch.float32),
+             (sr.LAST_BLOCK | sr.CLUSTER(1), {"grid": 8192, "block_threads": 128}, torch.float32)]
+    for variant, kw, odt in cases:
+        cfg = sr.make_config(variant, **kw)
+        ref = torch.empty((), dtype=odt, device="cuda")
+        sr.check(sr.reduce_sum_ptr(dfx.data_ptr(), n, sr.F32, ref.data_ptr(), cfg))
+        for _ in range(2):
+            out = torch.full((), -7, dtype=odt, device="cuda")
+            sr.check(sr.reduce_sum_noalloc_ptr(dfx.data_ptr(), n, sr.F32, out.data_ptr(), cfg))
+            torch.cuda.synchronize()
+            got = float(out.item())
+            assert abs(got - exact) <= bound, (hex(variant), kw, got, exact)
+            assert abs(got - float(ref.item())) <= bound, (hex(variant), kw)
+        refi = torch.empty((), dtype=torch.int64, device="cuda")
+        sr.check(sr.reduce_sum_ptr(dix.data_ptr(), n, sr.I32, refi.data_ptr(), cfg))
+        outi = torch.full((), -7, dtype=torch.int64, device="cuda")
+        sr.check(sr.reduce_sum_noalloc_ptr(dix.data_ptr(), n, sr.I32, outi.data_ptr(), cfg))
+        torch.cuda.synchronize()
+        assert int(outi.item()) == int(refi.item()) == oracle.sum_i32(xi), (hex(variant), kw)
