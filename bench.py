@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=N_HEADLINE, help="elements (profiling runs use a smaller case)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="input dtype of the timed loop (profiling runs of the precision path; the headline is f32)")
     ap.add_argument("--skip-extras", action="store_true", help="headline loop only (profiling runs)")
     ap.add_argument("--suite", default=None, choices=["selector", "barrier", "precision", "sweep", "segmented", "shapes", "seglayouts",
                              "latency"],
@@ -253,18 +255,27 @@ def main():
     variant = sr.AUTO if args.variant is None else args.variant
     cfg = sr.make_config(variant)
     N = args.n
-    resolved = sr.plan(N, sr.F32, cfg)
+    DT = {"f32": sr.F32, "bf16": sr.BF16, "fp8": sr.FP8E4M3}[args.dtype]
+    ES = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
+    if DT == sr.FP8E4M3:
+        cfg.scale = 1.0
+    resolved = sr.plan(N, DT, cfg)
     stage = resolved.variant & sr.STAGE_MASK
     launches_per_step = 2 if stage == sr.TWO_KERNEL else 1
 
     x_host = workloads.uniform_f32(N, seed=0)
-    x = torch.from_numpy(x_host).to(dev)
-    out = torch.empty((), dtype=torch.float32, device=dev)
+    if DT == sr.BF16:      # the same values rounded to BF16 / E4M3 (profiling runs)
+        x = torch.from_numpy(workloads.to_bf16_bits(x_host).view(np.int16)).to(dev)
+    elif DT == sr.FP8E4M3:
+        x = torch.from_numpy(workloads.to_e4m3_codes(x_host, scale=448.0)[0]).to(dev)
+    else:
+        x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty(2, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
 
     def step():
-        sr.check(sr.reduce_sum_ptr(x.data_ptr(), N, sr.F32, out.data_ptr(), cfg, sh))
+        sr.check(sr.reduce_sum_ptr(x.data_ptr(), N, DT, out.data_ptr(), cfg, sh))
 
     for _ in range(args.warmup):
         step()
@@ -312,7 +323,7 @@ def main():
         elapsed_ms = float(t.item())
     assert sr.stream_status(sh) == sr.OK
 
-    bytes_step = N * 4
+    bytes_step = N * ES
     value = ws * args.steps * bytes_step / (elapsed_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     # the dominant kernel's average launch duration: the timed region divided by
@@ -336,7 +347,7 @@ def main():
 
     # ---- secondary: latency at 2^14 (device time per call inside a graph of calls)
     secondary, e2e = None, None
-    if not args.skip_extras:
+    if not args.skip_extras and DT == sr.F32:   # the secondary legs are FP32 by definition
         secondary = {}
         try:
             secondary["latency_2p14_us"] = latency_small(sr, torch, dev, stream)
@@ -361,15 +372,15 @@ def main():
             e2e["value"] = float(t.item()) * ws
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.skip_extras:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.skip_extras and DT == sr.F32:
         cpu = cpu_baseline(args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD if N == N_HEADLINE else "device-wide sum, n=%d FP32 U[-1,1] seed 0" % N, "n": N, "variant": "0x%x" % resolved.variant,
+                "config": {"workload": WORKLOAD if (N == N_HEADLINE and DT == sr.F32) else "device-wide sum, n=%d %s U[-1,1] seed 0" % (N, args.dtype.upper()), "n": N, "variant": "0x%x" % resolved.variant,
                            "stage": sr.STAGE_NAMES.get(stage), "grid": resolved.grid,
                            "block": resolved.block_threads, "vec_bytes": resolved.vec_bytes,
                            "unroll": resolved.unroll, "tile_bytes": resolved.tile_bytes,

@@ -109,22 +109,34 @@ def barrier_suite(args):
                                                                 for k, v in r.items()}})
         except sr.SRError as e:
             _emit({"suite": "barrier", "level": level, **kw, "error": str(e)})
+    iters = 100_000      # back-to-back syncs per measurement (r1; the differential's r2 = r1 / 10)
+
+    def block_counts(threads):
+        """1, 2, 4, ... up to one CTA per SM, the SM count itself, then whole
+        waves of 2, 4, 8, ... CTAs per SM up to what is resident at once."""
+        out = [b for b in (1, 2, 4, 8, 16, 32, 64, 128) if b < sms] + [sms]
+        k = 2
+        while k * threads <= 2048 and k <= 32:
+            out.append(k * sms)
+            k *= 2
+        return out
     for g in (1, 2, 4, 8, 16, 32):
-        run(sr.LEVEL_WARP, group=g)
+        run(sr.LEVEL_WARP, group=g, iters=iters)
+    for blocks in block_counts(1024):
+        run(sr.LEVEL_WARP, group=32, blocks=blocks, threads=1024, iters=iters)
     for g in (1, 2, 7, 16, 31, 32):
-        run(sr.LEVEL_COALESCED, group=g)
-    run(sr.LEVEL_SHUFFLE)
-    for t in (32, 64, 128, 256, 512, 1024):
-        run(sr.LEVEL_BLOCK, threads=t)
-    for blocks, t in ((sms, 1024), (2 * sms, 1024), (4 * sms, 512), (8 * sms, 256)):
-        run(sr.LEVEL_BLOCK, blocks=blocks, threads=t, iters=20000)   # throughput with many warps per SM
+        run(sr.LEVEL_COALESCED, group=g, iters=iters)
+    run(sr.LEVEL_SHUFFLE, iters=iters)
+    for t in (32, 128, 256, 1024):                     # Section V-B: block sync against active warps
+        for blocks in block_counts(t):
+            run(sr.LEVEL_BLOCK, blocks=blocks, threads=t, iters=iters)
     for c in (2, 4, 8, 16):
         for t in (128, 1024):
-            run(sr.LEVEL_CLUSTER, cluster=c, threads=t, blocks=c)
-    for per_sm in (1, 2, 4, 8):
-        for t in (32, 128, 256, 512, 1024):
-            if per_sm * t <= 2048:
-                run(sr.LEVEL_GRID, blocks=per_sm * sms, threads=t, iters=20000)
+            for blocks in sorted({c, 8 * c, c * (sms // c)}):
+                run(sr.LEVEL_CLUSTER, cluster=c, threads=t, blocks=blocks, iters=iters)
+    for t in (32, 128, 256, 512, 1024):                # Section V-C: grid sync over blocks/SM x threads/block
+        for blocks in block_counts(t):
+            run(sr.LEVEL_GRID, blocks=blocks, threads=t, iters=iters)
     for kind in (sr.LAUNCH_TRADITIONAL, sr.LAUNCH_COOPERATIVE, sr.LAUNCH_CLUSTER):   # Table I
         run(sr.LEVEL_KERNEL, reps=20, method=kind)
     run(sr.LEVEL_KERNEL, reps=20, method=sr.LAUNCH_COOPERATIVE, blocks=sms)
@@ -292,7 +304,7 @@ def sweep_suite(args):
 
     fl_ms = graph_time(lambda: flush.fill_(1), 20)
     for dt, src in (("f32", big), ("i32", bigi)):
-        for k in range(10, 31, 2):
+        for k in range(10, 31):
             n = 1 << k
             x = src[:n]
             calls = 200 if k <= 20 else (20 if k <= 26 else 4)

@@ -283,6 +283,71 @@ template <int W> struct AccVec<kDtFP8, float, W> {
     }
 };
 
+// Compensated FP8: the vector's values sum exactly (as above); one TwoSum
+// carries the sum into the compensated accumulator 0.
+template <int W> struct AccVec<kDtFP8, Pair, W> {
+    __device__ static __forceinline__ void run(Pair (&a)[W], const uint32_t (&v)[W]) {
+        acc_add_f(a[0], AccVec<kDtFP8, float, W>::vec_sum(v));
+    }
+};
+
+// Two TwoSum accumulations at once in packed binary32 arithmetic (PTX
+// add/sub.rn.f32x2, sm_100+): lane k computes s_k + v_k = t_k + e_k exactly
+// (Knuth's TwoSum, each lane rounded to nearest like the scalar form) and
+// adds e_k into c_k.  Half the issue slots of two scalar TwoSums.
+__device__ __forceinline__ void two_sum2(float& s0, float& s1, float& c0, float& c1, float v0, float v1) {
+    asm("{ .reg .b64 s, v, t, bp, ap, d1, d2, e, c;\n"
+        " mov.b64 s, {%0, %1};\n mov.b64 c, {%2, %3};\n mov.b64 v, {%4, %5};\n"
+        " add.rn.f32x2 t, s, v;\n sub.rn.f32x2 bp, t, s;\n sub.rn.f32x2 ap, t, bp;\n"
+        " sub.rn.f32x2 d1, s, ap;\n sub.rn.f32x2 d2, v, bp;\n add.rn.f32x2 e, d1, d2;\n"
+        " add.rn.f32x2 c, c, e;\n"
+        " mov.b64 {%0, %1}, t;\n mov.b64 {%2, %3}, c; }"
+        : "+f"(s0), "+f"(s1), "+f"(c0), "+f"(c1)
+        : "f"(v0), "f"(v1));
+}
+
+// Compensated BF16: both halves of words w and w + 1 are widened exactly with
+// integer operations (BF16 is the top half of a binary32) and accumulated two
+// words at a time in packed arithmetic; each word accumulator still takes its
+// low half, then its high half, so the result is that of the scalar form.
+template <int W> struct AccVec<kDtBF16, Pair, W> {
+    __device__ static __forceinline__ void run(Pair (&a)[W], const uint32_t (&v)[W]) {
+#pragma unroll
+        for (int w = 0; w < W; w += 2) {
+            two_sum2(a[w].s, a[w + 1].s, a[w].c, a[w + 1].c, __uint_as_float(v[w] << 16),
+                     __uint_as_float(v[w + 1] << 16));
+            two_sum2(a[w].s, a[w + 1].s, a[w].c, a[w + 1].c, __uint_as_float(v[w] & 0xffff0000u),
+                     __uint_as_float(v[w + 1] & 0xffff0000u));
+        }
+    }
+};
+
+// One batch of U loaded vectors into the accumulators: vector by vector,
+// except FP8, whose values sum exactly in groups of up to 16 words (64
+// values, below the 73 that always sum exactly): one addition per group.
+template <int DT, class A, int W, int U> struct AccBatch {
+    __device__ static __forceinline__ void run(A (&a)[W], const uint32_t (&v)[U][W]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) AccVec<DT, A, W>::run(a, v[u]);
+    }
+};
+template <class A, int W, int U> struct AccBatch<kDtFP8, A, W, U> {
+    static constexpr int kGroup = (16 / W) < U ? (16 / W) : U;  // vectors per exact group
+    __device__ static __forceinline__ void run(A (&a)[W], const uint32_t (&v)[U][W]) {
+#pragma unroll
+        for (int g = 0; g < U; g += kGroup) {
+            float t[kGroup];
+#pragma unroll
+            for (int k = 0; k < kGroup; ++k) t[k] = AccVec<kDtFP8, float, W>::vec_sum(v[g + k]);
+#pragma unroll
+            for (int s = kGroup / 2; s >= 1; s >>= 1)
+#pragma unroll
+                for (int k = 0; k < s; ++k) t[k] = __fadd_rn(t[k], t[k + s]);
+            acc_add_f(a[0], t[0]);
+        }
+    }
+};
+
 // Dependent additions made into one word accumulator by one acc_word call.
 template <int DT> struct AddsPerWord { static constexpr int v = 1; };   // F32, I32; FP8 (a vector sums exactly first)
 template <> struct AddsPerWord<kDtBF16> { static constexpr int v = 2; };

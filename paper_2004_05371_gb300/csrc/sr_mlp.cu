@@ -15,6 +15,7 @@
 #include <cstring>
 #include <vector>
 
+#include "sr_device.cuh"
 #include "sr_internal.h"
 
 namespace sr {
@@ -199,6 +200,11 @@ __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(MlpDims d, const 
     __shared__ float red[kParts][kMaxH];
     const int tid = threadIdx.x, col = tid & (kMaxH - 1), part = tid / kMaxH;
     const int k1 = (d.in + kParts - 1) / kParts, k2 = (d.h + kParts - 1) / kParts;
+    // launched with programmatic stream serialisation: wait for the previous
+    // kernel (a training step may have just written the parameters) before
+    // any global read; only the launch latency overlaps
+    grid_dependency_wait();
+    allow_dependents();
     float w1[kR1], w2[kR2], w3[kR2];
 #pragma unroll
     for (int r = 0; r < kR1; ++r) {
@@ -389,7 +395,22 @@ int sr_mlp_train_step(sr_mlp h, const float* X, const float* Q, int batch, float
 int sr_mlp_predict(sr_mlp h, const float* X, int batch, int* cls, float* logits, sr_stream_t stream) {
     if (!h || !X || !cls || batch < 1) return SR_ERR_ARG;
     const int blocks = batch < 4096 ? batch : 4096;  // one CTA per sample, grid-stride beyond
-    mlp_predict_kernel<<<blocks, kThreads, 0, (cudaStream_t)stream>>>(h->d, h->params, X, batch, cls, logits);
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof lc);
+    lc.gridDim = dim3(blocks);
+    lc.blockDim = dim3(kThreads);
+    lc.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const MlpDims dd = h->d;
+    const float* prm = h->params;
+    void* args[] = {const_cast<MlpDims*>(&dd), const_cast<float**>(&prm), const_cast<float**>(&X), &batch, &cls,
+                    &logits};
+    cudaError_t le = cudaLaunchKernelExC(&lc, (const void*)mlp_predict_kernel, args);
+    if (le != cudaSuccess) return status_from_cuda(le);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SR_OK : status_from_cuda(e);
 }

@@ -25,9 +25,11 @@ constexpr int kKnownFlags = SR_STAGE_MASK | SR_CLUSTER_MASK | SR_F_KAHAN | SR_F_
                             SR_F_HOST_DIRECT | SR_F_FP64_AUTO;
 // SR_AUTO's launch shapes, from graph-timed size sweeps and autotuner sweeps
 // on a GB300 (device time per call in a CUDA graph, FP32):
-//   <= 16 KiB : one CTA of 256 threads, 32 B x 2 loads, no grid stage (1.6 us)
-//   <= 1 MiB  : one cluster of 16 such CTAs, DSMEM merge, no grid stage
-//               (1.8 us at 64 KiB, 2.4 at 1 MiB)
+//   <= 32 KiB : one CTA, one 16 B x 2 batch per thread, no grid stage
+//               (1.26 us at 4 KiB, 1.40 at 16 KiB)
+//   <= 1 MiB  : a cluster of up to 16 CTAs of at least 256 threads, one
+//               batch per thread, DSMEM merge, no grid stage (1.74 us at
+//               64 KiB, 1.96 at 256 KiB, 2.47 at 1 MiB with four loads)
 //   <= 64 MiB : two-kernel form, grid sized by the work, 32 B loads (2.9 us at
 //               4 MiB, 3.5 at 16 MiB, 6.4 at 64 MiB with the input in L2)
 //   larger    : per dtype, below: the two-kernel form with 16 B loads up to
@@ -40,7 +42,6 @@ struct AutoShape {
     bool bulk;
     int tile, stages;
 };
-constexpr int64_t kAutoOneCtaBytes = 16 << 10;
 constexpr int64_t kAutoClusterBytes = 1 << 20;
 constexpr int64_t kAutoTwoKernelBytes = 64 << 20;
 constexpr int64_t kAutoLdgBytes = 512 << 20;
@@ -59,10 +60,12 @@ AutoShape auto_large_shape(int dtype, bool comp, int64_t bytes, bool allow_bulk)
         if (dtype == SR_F32)
             return ldg ? AutoShape{SR_TWO_KERNEL, 1024, 16, 1, false, 0, 0}
                        : AutoShape{SR_LAST_BLOCK, 544, 16, 4, true, 32 << 10, 4};
-        if (dtype == SR_BF16)
-            return ldg ? AutoShape{SR_TWO_KERNEL, 1024, 16, 1, false, 0, 0}
-                       : AutoShape{SR_LAST_BLOCK, 544, 16, 4, true, 64 << 10, 3};
-        return {SR_LAST_BLOCK, 1024, 16, 2, false, 0, 0};  // FP8: four values per word sum exactly
+        if (dtype == SR_BF16)  // packed TwoSum: two loads in flight keep pace up to 1 GiB
+            return ldg || bytes <= ((int64_t)1 << 30) ? AutoShape{SR_TWO_KERNEL, 1024, 16, 2, false, 0, 0}
+                                                      : AutoShape{SR_LAST_BLOCK, 544, 16, 4, true, 64 << 10, 3};
+        // FP8: a vector's 16 values sum exactly, one TwoSum per vector
+        return ldg ? AutoShape{SR_TWO_KERNEL, 1024, 16, 1, false, 0, 0}
+                   : AutoShape{SR_LAST_BLOCK, 544, 16, 1, true, 64 << 10, 3};
     }
     if (dtype == SR_BF16)
         return ldg ? AutoShape{SR_TWO_KERNEL, 512, 16, 2, false, 0, 0}
@@ -136,11 +139,26 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
         const int64_t bytes = n * p.elem;
         const bool chosen_cluster = p.log2c != 0;
         if (bytes <= kAutoClusterBytes) {
+            // one 16 B x 2 batch (32 bytes) per thread: one CTA of up to 1024
+            // threads, then a cluster of up to 16 CTAs of at least 256
+            // threads, then four loads per thread (warm / cold graph sweeps
+            // of every shape, 2^10..2^18 FP32)
             p.stage = SR_SINGLE_CLUSTER;
-            if (!chosen_cluster) p.log2c = bytes <= kAutoOneCtaBytes ? 0 : 4;
-            def_block = 256;
-            def_vec = 32;
+            def_vec = 16;
             def_unroll = 2;
+            const int64_t threads = std::max<int64_t>(32, cdiv(bytes, 32));
+            int log2c = 0;
+            if (threads > 1024) {
+                while (log2c < 4 && ((int64_t)256 << (log2c + 1)) <= threads) ++log2c;
+            }
+            if (chosen_cluster) log2c = p.log2c;
+            else p.log2c = log2c;
+            int64_t per_cta = cdiv(threads, (int64_t)1 << log2c);
+            if (per_cta > 1024) {
+                def_unroll = 4;
+                per_cta = cdiv(per_cta, 2);
+            }
+            def_block = (int)std::min<int64_t>(1024, cdiv(per_cta, 32) * 32);
         } else if (bytes <= kAutoTwoKernelBytes) {
             p.stage = SR_TWO_KERNEL;
             if (!p.comp) {

@@ -12,10 +12,11 @@ pytestmark = pytest.mark.gpu
 
 
 def test_plan_auto_regimes(sr):
-    """SR_AUTO: one CTA up to 16 KiB, a 16-CTA cluster up to 1 MiB, the
-    two-kernel form up to 512 MiB, then last-block-done on the TMA ring
-    (FP32 sizes; the ring's shape per dtype)."""
-    cases = [(1 << 10, sr.SINGLE_CLUSTER, 0), (1 << 12, sr.SINGLE_CLUSTER, 0), (1 << 14, sr.SINGLE_CLUSTER, 4),
+    """SR_AUTO: one CTA up to 32 KiB and a cluster of up to 16 CTAs up to
+    1 MiB (one 16 B x 2 batch per thread), the two-kernel form up to 512 MiB,
+    then last-block-done on the TMA ring (FP32 sizes; the ring's shape per
+    dtype)."""
+    cases = [(1 << 10, sr.SINGLE_CLUSTER, 0), (1 << 12, sr.SINGLE_CLUSTER, 0), (1 << 14, sr.SINGLE_CLUSTER, 3),
              (1 << 18, sr.SINGLE_CLUSTER, 4), (1 << 20, sr.TWO_KERNEL, 0), (1 << 24, sr.TWO_KERNEL, 0),
              (1 << 26, sr.TWO_KERNEL, 0), (1 << 27, sr.TWO_KERNEL, 0), (1 << 28, sr.LAST_BLOCK, 0)]
     for n, stage, log2c in cases:
@@ -24,6 +25,10 @@ def test_plan_auto_regimes(sr):
         assert (r.variant & sr.CLUSTER_MASK) >> sr.CLUSTER_SHIFT == log2c, n
     r = sr.plan(1 << 27, sr.F32)
     assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 1, 512) and not r.variant & sr.F_BULK
+    for n, shape in (((1 << 10), (1, 128, 2)), ((1 << 12), (1, 512, 2)), ((1 << 14), (8, 256, 2)),
+                     ((1 << 16), (16, 512, 2)), ((1 << 18), (16, 1024, 4))):
+        r = sr.plan(n, sr.F32)
+        assert (r.grid, r.block_threads, r.unroll, r.vec_bytes) == shape + (16,), (n, r.as_dict())
     r = sr.plan(1 << 28, sr.F32)
     assert r.variant & sr.F_BULK and (r.tile_bytes, r.stages, r.block_threads) == (65536, 2, 288)
     r = sr.plan(1 << 28, sr.I32)
