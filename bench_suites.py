@@ -401,7 +401,8 @@ def seglayouts_suite(args):
     default kernel and SR_F_DENSE_SEGMENTS in two launch shapes, the TMA
     form (SR_F_BULK, 256 threads, chunks of 4 rows, 2 stages) and the
     warp-per-segment form (SR_F_WARP_SEGMENTS, 16 B x 4 and 16 B x 2) and the
-    thread-per-segment form (SR_F_LANE_SEGMENTS, 4 loads per step); atomic finish;
+    thread-per-segment form (SR_F_LANE_SEGMENTS, 4 loads per step) and the
+    adaptive form (SR_F_ADAPTIVE_SEGMENTS); atomic finish where a form has one;
     device time per call in a CUDA graph."""
     import torch
     import paper_2004_05371_gb300 as sr
@@ -422,7 +423,7 @@ def seglayouts_suite(args):
              "ldg512": ((512, 32, 4), 0), "dense512": ((512, 32, 4), sr.F_DENSE_SEGMENTS),
              "tma": ((256, 32, 4), sr.F_BULK), "warp16": ((256, 16, 4), sr.F_WARP_SEGMENTS),
              "warp16u2": ((256, 16, 2), sr.F_WARP_SEGMENTS), "lane": ((256, 16, 4), sr.F_LANE_SEGMENTS),
-             "lane32": ((256, 32, 4), sr.F_LANE_SEGMENTS)}
+             "lane32": ((256, 32, 4), sr.F_LANE_SEGMENTS), "adaptive": ((256, 16, 2), sr.F_ADAPTIVE_SEGMENTS)}
     only = getattr(args, "layout", None)
     form = getattr(args, "seg_form", None)
     for name, off in cases:
@@ -447,6 +448,7 @@ def seglayouts_suite(args):
             _emit({"suite": "seglayouts", "layout": name, "nseg": nseg, "n": n,
                    "dense": bool(flags & sr.F_DENSE_SEGMENTS), "bulk": bool(flags & sr.F_BULK),
                    "warp": bool(flags & sr.F_WARP_SEGMENTS), "lane": bool(flags & sr.F_LANE_SEGMENTS),
+                   "adaptive": bool(flags & sr.F_ADAPTIVE_SEGMENTS),
                    "shape": "%d threads x %d B x unroll %d" % shape,
                    "ran": "%d threads x %d B x unroll %d%s" % (r.block_threads, r.vec_bytes, r.unroll,
                                                                ", %d stages" % r.stages if r.stages else ""),

@@ -122,6 +122,22 @@ typedef enum {
                                    (1/2/4/8, default 4) per step.  For very short segments.  No grid stage;
                                    deterministic.  Not with another form flag
                                    (SR_ERR_UNSUPPORTED).  The paper has no counterpart. */
+#define SR_F_ADAPTIVE_SEGMENTS 0x10000 /* segmented only: one cooperative launch for any
+                                   layout.  The segments are partitioned by length on the
+                                   device: segments of at most 512 bytes are summed by
+                                   single lanes, longer ones up to one chunk by whole warps
+                                   (as SR_F_WARP_SEGMENTS), and each longer segment is cut
+                                   into chunks (at least 64 KiB of input, at least 2 x
+                                   the total / 98304) queued in the workspace; after
+                                   grid.sync() every warp takes chunks from the queue and
+                                   the last chunk of a segment to finish combines its
+                                   partials in chunk order.  No grid-stage variant is
+                                   used; deterministic.  Shape fields other than grid
+                                   must be 0 or the defaults (16-byte vectors, unroll 2,
+                                   256 threads; else SR_ERR_UNSUPPORTED); an explicit grid
+                                   that cannot be co-resident -> SR_ERR_LAUNCH.  Not with
+                                   another form flag.  The paper has no counterpart (its
+                                   grid.sync, Section III-A-3, joins the two phases). */
 #define SR_F_HOST_DIRECT 0x800  /* sr_reduce_sum_host only: the kernel reads the host
                                    array in place over the CPU-GPU link (page-locked
                                    memory, or any memory where the device accesses
@@ -274,13 +290,17 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * with 32768 or more segments take the TMA form, fewer the LDG one.
  * With SR_F_WARP_SEGMENTS whole segments go to single warps instead, with
  * SR_F_LANE_SEGMENTS to single threads (see the flags): no segment is split,
- * the stage bits are ignored and the results are deterministic.
+ * the stage bits are ignored and the results are deterministic.  With
+ * SR_F_ADAPTIVE_SEGMENTS one cooperative launch partitions the segments by
+ * length on the device (lanes, warps, queued chunks; see the flag): the stage
+ * bits are ignored and the results are deterministic.
  * cfg fields used: variant (stage, SR_F_KAHAN, SR_F_FP64_COMBINE, SR_F_BULK,
- * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS, SR_F_LANE_SEGMENTS),
+ * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS, SR_F_LANE_SEGMENTS, SR_F_ADAPTIVE_SEGMENTS),
  * block_threads (at most 512), ctas_per_sm, grid (at most 65536 warps in
  * total), vec_bytes, unroll, stages (TMA form), scale (FP8).
  * SR_SINGLE_CLUSTER, cluster bits, and any two of SR_F_BULK,
- * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS and SR_F_LANE_SEGMENTS ->
+ * SR_F_DENSE_SEGMENTS, SR_F_WARP_SEGMENTS, SR_F_LANE_SEGMENTS and
+ * SR_F_ADAPTIVE_SEGMENTS ->
  * SR_ERR_UNSUPPORTED; a ring larger than a CTA's shared memory ->
  * SR_ERR_LAUNCH.
  * Errors: SR_ERR_ARG (nseg < 0, NULL pointer with nseg > 0, misalignment,

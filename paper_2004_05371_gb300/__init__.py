@@ -28,6 +28,7 @@ F_FP64_AUTO = 0x1000
 F_DENSE_SEGMENTS = 0x2000
 F_WARP_SEGMENTS = 0x4000  # segmented: whole segments per warp, no grid stage
 F_LANE_SEGMENTS = 0x8000  # segmented: whole segments per thread, no grid stage
+F_ADAPTIVE_SEGMENTS = 0x10000  # segmented: one cooperative launch, partition by length on the device
 # status codes (sr_status)
 OK, ERR_ARG, ERR_DTYPE, ERR_LAUNCH, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 # barrier levels (sr_level)

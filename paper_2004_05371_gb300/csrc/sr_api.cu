@@ -398,6 +398,7 @@ int sr_stream_status(sr_stream_t stream) {
     }
     if (err & kErrTimeout) return SR_ERR_TIMEOUT;
     if (err & kErrBadOffsets) return SR_ERR_ARG;
+    if (err & kErrQueueFull) return SR_ERR_LAUNCH;
     if (err) return SR_ERR_LAUNCH;
     return SR_OK;
 }

@@ -17,7 +17,7 @@ namespace sr {
 //   seg          : segmented-reduction carries
 constexpr int kMaxUnits = 65536;
 constexpr size_t kSlotBytes = 16;
-constexpr size_t kSegBytes = 4u << 20;
+constexpr size_t kSegBytes = 8u << 20;  // also holds the adaptive form's chunk queue (sr_segparams.h)
 // Segmented carries: tickets (4 B), last_seg (8 B), carry_first and
 // carry_last (16 B each) per warp: 44 B x 65536 warps = 2.75 MiB <= kSegBytes.
 constexpr int64_t kSegMaxWarps = 65536;
@@ -64,7 +64,7 @@ struct SegPlan {
     int dtype = 0;
     int64_t nseg = 0;
     int stage = 0;
-    bool comp = false, fp64 = false, dense = false, bulk = false, warp = false, lane = false;
+    bool comp = false, fp64 = false, dense = false, bulk = false, warp = false, lane = false, adapt = false;
     int vec = 16, unroll = 4, block = 256, grid = 0;
     int stages = 0;
     size_t smem = 0;  // dynamic shared memory of the TMA form

@@ -29,10 +29,21 @@ __global__ void __launch_bounds__(256) seg_check_kernel(const int64_t* offsets, 
 }
 constexpr int kKnownSegFlags =
     SR_STAGE_MASK | SR_F_KAHAN | SR_F_FP64_COMBINE | SR_F_DENSE_SEGMENTS | SR_F_BULK | SR_F_WARP_SEGMENTS |
-    SR_F_LANE_SEGMENTS;
+    SR_F_LANE_SEGMENTS | SR_F_ADAPTIVE_SEGMENTS;
 // the load-path / form flags, at most one of which a segmented call may set
-constexpr int kSegFormFlags = SR_F_DENSE_SEGMENTS | SR_F_BULK | SR_F_WARP_SEGMENTS | SR_F_LANE_SEGMENTS;
+constexpr int kSegFormFlags =
+    SR_F_DENSE_SEGMENTS | SR_F_BULK | SR_F_WARP_SEGMENTS | SR_F_LANE_SEGMENTS | SR_F_ADAPTIVE_SEGMENTS;
 constexpr int64_t kSegBulkMin = 32768;  // segments from which the default shape is the TMA form
+
+const void* seg_adapt_kernel(int dtype, bool comp, int vec, int unroll) {
+    switch (dtype) {
+    case SR_F32: return seg_adapt_f32(comp, vec, unroll);
+    case SR_I32: return seg_adapt_i32(comp, vec, unroll);
+    case SR_BF16: return seg_adapt_bf16(comp, vec, unroll);
+    case SR_FP8E4M3: return seg_adapt_fp8(comp, vec, unroll);
+    default: return nullptr;
+    }
+}
 
 bool seg_kernels(int dtype, bool comp, int vec, int unroll, bool dense, bool bulk, bool warp, bool lane,
                  const void** main, const void** fin) {
@@ -119,6 +130,32 @@ int seg_plan(int64_t nseg, int dtype, const sr_config& c, const DeviceInfo& d, S
         p.vec = c.vec_bytes ? c.vec_bytes : 16;
         p.unroll = c.unroll ? c.unroll : 2;
     }
+    p.adapt = (c.variant & SR_F_ADAPTIVE_SEGMENTS) != 0;
+    if (p.adapt) {
+        // one cooperative launch of the resident number of 256-thread CTAs;
+        // phase 1 at the warp form's shape (16-byte vectors, 2 per lane)
+        if ((c.vec_bytes && c.vec_bytes != 16) || (c.unroll && c.unroll != 2) ||
+            (c.block_threads && c.block_threads != 256))
+            return SR_ERR_UNSUPPORTED;
+        p.vec = 16;
+        p.unroll = 2;
+        p.block = 256;
+        p.main = seg_adapt_kernel(dtype, p.comp, p.vec, p.unroll);
+        p.fin = nullptr;
+        if (!p.main) return SR_ERR_UNSUPPORTED;
+        int st = prepare_function(p.main, 0, false);
+        if (st != SR_OK) return st;
+        int resident = 0;
+        st = blocks_per_sm(d, p.main, p.block, 0, &resident);
+        if (st != SR_OK) return st;
+        if (resident < 1) return SR_ERR_LAUNCH;
+        int64_t grid = c.grid ? c.grid : (int64_t)resident * d.sms;
+        if (grid > (int64_t)resident * d.sms) return SR_ERR_LAUNCH;  // could not be co-resident
+        p.grid = (int)std::max<int64_t>(1, grid);
+        p.warps = (int64_t)p.grid * (p.block / 32);
+        *out = p;
+        return SR_OK;
+    }
     if (p.dense) {  // the dense kernel runs at most 4 rows in flight; 512-thread CTAs by default
         if (p.unroll > 4) p.unroll = 4;
         if (!c.block_threads) p.block = 512;
@@ -195,6 +232,20 @@ int seg_launch(const void* x, const int64_t* offsets, void* out, const SegPlan& 
     kp.stage = p.stage;
     kp.fp64 = p.fp64 ? 1 : 0;
     cudaError_t e;
+    if (p.adapt) {
+        // the chunk queue: counters at the head of the tickets (the last warp
+        // of each launch resets them to zero), arrays after the tickets
+        SegQueue kq;
+        kq.ctr = reinterpret_cast<unsigned int*>(ws.seg);
+        unsigned char* q = ws.seg + (size_t)kSegMaxWarps * 4;
+        kq.desc = reinterpret_cast<long long*>(q);
+        kq.part = q + (size_t)kAdaptQueueCap * 16;
+        kq.tick = reinterpret_cast<unsigned int*>(q + (size_t)kAdaptQueueCap * 32);
+        kq.cap = kAdaptQueueCap;
+        void* aargs[] = {&kp, &kq};
+        e = cudaLaunchCooperativeKernel(p.main, dim3(p.grid), dim3(p.block), aargs, 0, s);
+        return e == cudaSuccess ? SR_OK : status_from_cuda(e);
+    }
     if (p.stage == SR_ATOMIC && !p.warp && !p.lane) {
         const size_t ob = (p.dtype == SR_I32 || p.fp64) ? 8 : 4;
         const int zs = launch_zero(out, ob * (size_t)p.nseg, s);

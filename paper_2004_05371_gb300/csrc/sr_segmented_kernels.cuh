@@ -707,12 +707,228 @@ inline const void* pick_seg_lane(int vec, int unroll) {
 // warp-wide path only for the long ones.
 constexpr int64_t kLaneAloneBytes = 512;  // segments a lane of the warp form sums alone
 
+// ------------------------------------------------------- adaptive form
+// SR_F_ADAPTIVE_SEGMENTS: one cooperative launch for any layout.  Phase 1
+// walks the segments in blocks as the warp form does and partitions them by
+// length on the device: segments of at most kLaneAloneBytes go to single
+// lanes, longer ones up to `thr` elements (kGroupMaxBytes, more for very
+// large inputs) to groups of kGroupLanes lanes, and every longer segment is
+// cut into chunks of `chunk` elements that are appended to a queue in the
+// workspace.  grid.sync(), then phase 2: every warp takes
+// chunks from the queue (one atomic per chunk) and sums them; the last chunk
+// of a segment to finish combines the segment's chunk partials in chunk order,
+// so the result does not depend on the order in which chunks were queued or
+// taken (deterministic); a segment of one chunk is written directly.
+
+// Queue the chunks of the block's long segments (whole warp calls).
+__device__ __forceinline__ void enqueue_chunks(const SegParams& p, const SegQueue& q, int64_t b0, int64_t o,
+                                               int64_t e, bool lng, int64_t chunk, int lane) {
+    unsigned pend = __ballot_sync(0xffffffffu, lng);
+    while (pend != 0u) {
+        const int L = __ffs(pend) - 1;
+        pend &= pend - 1u;
+        const int64_t so = __shfl_sync(0xffffffffu, o, L);
+        const int64_t se = __shfl_sync(0xffffffffu, e, L);
+        const int64_t k = (se - so + chunk - 1) / chunk;
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(q.ctr, (unsigned)k);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)base + k <= q.cap) {
+            for (int64_t j = lane; j < k; j += 32) {
+                q.desc[2 * ((int64_t)base + j)] = b0 + L;
+                q.desc[2 * ((int64_t)base + j) + 1] = (j << 32) | k;
+            }
+            if (lane == 0) q.tick[base] = 0u;
+        } else if (lane == 0) {
+            atomicOr(p.err, kErrQueueFull);
+        }
+    }
+}
+
+// Adaptive form, mid-length segments: groups of kGroupLanes lanes, one
+// segment per group, kGroupLanes / 32 segments per warp pass.  A load
+// instruction of the warp then covers four 128-byte runs of four segments,
+// and the fixed costs of a segment (offsets, head and tail, reduction) are
+// shared by a quarter of the warp instead of all of it.
+constexpr int kGroupLanes = 8;
+constexpr int64_t kGroupMaxBytes = 8 << 10;  // longer ones: the whole warp, two at a time
+
+// x[s0, s1) summed by the kGroupLanes lanes of a group (gl = lane in group):
+// head and tail elements singly, the VB-aligned body strided over the group,
+// UNROLL vectors per lane in flight.  Returns the lane's partial (reduce over
+// the group afterwards, with the whole warp converged).
 template <int DT, bool COMP, int VB, int UNROLL>
-__global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
+__device__ __forceinline__ typename Acc<DT, COMP>::T group_range_part(const unsigned char* x, int64_t s0,
+                                                                       int64_t s1, int gl) {
+    using A = typename Acc<DT, COMP>::T;
+    constexpr int EB = SegElem<DT>::v;
+    constexpr int PV = VB / EB;
+    constexpr int W = VB / 4;
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x);
+    int64_t a0 = s0 + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0 * EB) % VB) % VB) / EB);
+    if (a0 > s1) a0 = s1;
+    const int64_t nv = (s1 - a0) / PV;
+    const int64_t a1 = a0 + nv * PV;
+    A edge = Op<A>::zero();
+    for (int64_t i = s0 + gl; i < a0; i += kGroupLanes) acc_elem<DT>(edge, x, i);
+    for (int64_t i = a1 + gl; i < s1; i += kGroupLanes) acc_elem<DT>(edge, x, i);
+    A acc[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[q] = Op<A>::zero();
+    const unsigned char* body = x + a0 * EB;
+    for (int64_t v0 = 0; v0 < nv; v0 += kGroupLanes * UNROLL) {
+        uint32_t r[UNROLL][W];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t v = v0 + u * kGroupLanes + gl;
+            if (v < nv) ldg_vec(body + v * VB, r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (v0 + u * kGroupLanes + gl < nv) AccVec<DT, A, W>::run(acc, r[u]);
+    }
+    return Op<A>::add(sum_words<A, W>(acc), edge);
+}
+
+// The block's mid-length segments (mask: lanes holding one), kGroupLanes
+// lanes per segment, 32 / kGroupLanes at a time (whole warp calls).
+template <int DT, bool COMP>
+__device__ __forceinline__ void group_segments(const SegParams& p, int64_t b0, int64_t o, int64_t e, unsigned mask,
+                                               int lane) {
+    using A = typename Acc<DT, COMP>::T;
+    constexpr int NG = 32 / kGroupLanes;
+    const int g = lane / kGroupLanes, gl = lane % kGroupLanes;
+    while (mask != 0u) {
+        // the next NG segments of the mask, one per group
+        int mine = -1;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            const int L = mask ? __ffs(mask) - 1 : -1;
+            if (L >= 0) mask &= mask - 1u;
+            if (k == g) mine = L;
+        }
+        const int src = mine < 0 ? 0 : mine;
+        const int64_t so = __shfl_sync(0xffffffffu, o, src);
+        const int64_t se = __shfl_sync(0xffffffffu, e, src);
+        A v = mine < 0 ? Op<A>::zero() : group_range_part<DT, COMP, 16, 4>(p.x, so, se, gl);
+#pragma unroll
+        for (int off = kGroupLanes / 2; off >= 1; off >>= 1) v = Op<A>::add(v, Op<A>::shfl_down(v, off));
+        if (gl == 0 && mine >= 0) seg_out(p, b0 + mine, v);
+    }
+}
+
+// One block of nb (<= 32) consecutive segments b0.. summed by one warp: lane
+// k holds offsets[b0 + k], so the block costs one coalesced offsets load.
+// Segments of at most kLaneAloneBytes are summed by their own lane; the rest
+// by the whole warp, two at a time.  ADAPT (the adaptive form): segments
+// longer than `thr` elements are queued as chunks of `chunk` elements, the
+// others beyond kLaneAloneBytes go to lane groups (no whole-warp path).
+template <int DT, bool COMP, int VB, int UNROLL, bool ADAPT>
+__device__ __forceinline__ void seg_warp_block(const SegParams& p, const SegQueue* q, int64_t b0, int64_t nb,
+                                               int lane, int64_t thr, int64_t chunk) {
     using A = typename Acc<DT, COMP>::T;
     constexpr int EB = SegElem<DT>::v;
     constexpr int PV = VB / EB;  // elements per lane vector
     constexpr int W = VB / 4;    // 32-bit words per lane vector
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(p.x);
+    const int64_t i = b0 + (lane < nb ? lane : nb);           // lane nb (or 31) holds the end
+    const int64_t o = __ldg(p.offsets + i);
+    const int64_t o_end = __ldg(p.offsets + b0 + nb);
+    // this lane's segment [o, e); the short ones are summed by their lane alone
+    const int64_t o_up = __shfl_down_sync(0xffffffffu, o, 1);
+    const bool mine = lane < nb;
+    const int64_t e = (lane + 1 < nb) ? o_up : o_end;
+    const bool alone = mine && (e - o) * EB <= kLaneAloneBytes;
+    if (alone) seg_out(p, b0 + lane, lane_sum<DT, COMP, 16, 4>(p.x, o, e));
+    if constexpr (ADAPT) {
+        // adaptive form: segments longer than `thr` elements go to the chunk
+        // queue, the others to lane groups
+        const bool lng = mine && (e - o) > thr;
+        enqueue_chunks(p, *q, b0, o, e, lng, chunk, lane);
+        group_segments<DT, COMP>(p, b0, o, e, __ballot_sync(0xffffffffu, mine && !alone && !lng), lane);
+        return;
+    }
+    // the rest by the whole warp, two at a time: both first batches of loads in flight together
+    unsigned todo = __ballot_sync(0xffffffffu, mine && !alone);
+    while (todo != 0u) {
+        const int k0 = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const bool two = todo != 0u;  // warp-uniform
+        const int k1 = two ? __ffs(todo) - 1 : k0;
+        if (two) todo &= todo - 1u;
+        int64_t s0[2], s1[2];
+        s0[0] = __shfl_sync(0xffffffffu, o, k0);
+        s1[0] = __shfl_sync(0xffffffffu, e, k0);
+        s0[1] = __shfl_sync(0xffffffffu, o, k1);
+        s1[1] = __shfl_sync(0xffffffffu, e, k1);
+        if (!two) s0[1] = s1[1] = s1[0];  // an empty second segment
+        int64_t a0[2], nv[2];
+        A edge[2], acc[2][W];
+        uint32_t r[2][UNROLL][W];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            a0[j] = s0[j] + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0[j] * EB) % VB) % VB) / EB);
+            if (a0[j] > s1[j]) a0[j] = s1[j];
+            nv[j] = (s1[j] - a0[j]) / PV;
+            const int64_t a1 = a0[j] + nv[j] * PV;
+            edge[j] = Op<A>::zero();  // head [s0, a0) and tail [a1, s1), fewer than PV each
+            if (lane < a0[j] - s0[j]) acc_elem<DT>(edge[j], p.x, s0[j] + lane);
+            if (lane < s1[j] - a1) acc_elem<DT>(edge[j], p.x, a1 + lane);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int64_t v = u * 32 + lane;
+                if (v < nv[j]) ldg_vec(p.x + (a0[j] + v * PV) * EB, r[j][u]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) acc[j][q] = Op<A>::zero();
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (u * 32 + lane < nv[j]) {
+#pragma unroll
+                    for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[j][u][q]);
+                }
+            }
+        }
+        // the rest of a segment longer than one batch, with both batch
+        // buffers free now: 2 * UNROLL vectors per lane in flight
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const unsigned char* body = p.x + a0[j] * EB;
+            for (int64_t v0 = 32 * UNROLL; v0 < nv[j]; v0 += 64 * UNROLL) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        const int64_t v = v0 + (h * UNROLL + u) * 32 + lane;
+                        if (v < nv[j]) ldg_vec(body + v * VB, r[h][u]);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        if (v0 + (h * UNROLL + u) * 32 + lane < nv[j]) {
+#pragma unroll
+                            for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[h][u][q]);
+                        }
+                    }
+                }
+            }
+        }
+        const A t0 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[0]), edge[0]));
+        const A t1 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[1]), edge[1]));
+        if (lane == 0) {
+            seg_out(p, b0 + k0, t0);
+            if (two) seg_out(p, b0 + k1, t1);
+        }
+    }
+}
+
+template <int DT, bool COMP, int VB, int UNROLL>
+__global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
     grid_dependency_wait();
     allow_dependents();
     if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // offsets failed the check: read nothing
@@ -721,98 +937,179 @@ __global__ void __launch_bounds__(512) seg_warp_kernel(const SegParams p) {
     const int64_t Wn = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t G = (p.nseg + Wn - 1) / Wn;
     G = G < 1 ? 1 : (G > 32 ? 32 : G);
-    const uintptr_t xa = reinterpret_cast<uintptr_t>(p.x);
-    for (int64_t b0 = w * G; b0 < p.nseg; b0 += Wn * G) {
-        const int64_t nb = (p.nseg - b0 < G) ? p.nseg - b0 : G;  // segments in this block
-        const int64_t i = b0 + (lane < nb ? lane : nb);           // lane nb (or 31) holds the end
-        const int64_t o = __ldg(p.offsets + i);
-        const int64_t o_end = __ldg(p.offsets + b0 + nb);
-        // this lane's segment [o, e); the short ones are summed by their lane alone
-        const int64_t o_up = __shfl_down_sync(0xffffffffu, o, 1);
-        const bool mine = lane < nb;
-        const int64_t e = (lane + 1 < nb) ? o_up : o_end;
-        const bool alone = mine && (e - o) * EB <= kLaneAloneBytes;
-        if (alone) seg_out(p, b0 + lane, lane_sum<DT, COMP, 16, 4>(p.x, o, e));
-        // the rest by the whole warp, two at a time: both first batches of loads in flight together
-        unsigned todo = __ballot_sync(0xffffffffu, mine && !alone);
-        while (todo != 0u) {
-            const int k0 = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            const bool two = todo != 0u;  // warp-uniform
-            const int k1 = two ? __ffs(todo) - 1 : k0;
-            if (two) todo &= todo - 1u;
-            int64_t s0[2], s1[2];
-            s0[0] = __shfl_sync(0xffffffffu, o, k0);
-            s1[0] = __shfl_sync(0xffffffffu, e, k0);
-            s0[1] = __shfl_sync(0xffffffffu, o, k1);
-            s1[1] = __shfl_sync(0xffffffffu, e, k1);
-            if (!two) s0[1] = s1[1] = s1[0];  // an empty second segment
-            int64_t a0[2], nv[2];
-            A edge[2], acc[2][W];
-            uint32_t r[2][UNROLL][W];
+    for (int64_t b0 = w * G; b0 < p.nseg; b0 += Wn * G)
+        seg_warp_block<DT, COMP, VB, UNROLL, false>(p, nullptr, b0, (p.nseg - b0 < G) ? p.nseg - b0 : G, lane, 0, 0);
+}
+
+// x[s0, s1) summed by one warp: the elements before the first VB-aligned
+// address and after the last whole vector singly by the first lanes, the
+// vectors between strided over the lanes, UNROLL per lane in flight; blocked
+// accumulation (Levels) in the plain binary32 form; warp reduction.
+template <int DT, bool COMP, int VB, int UNROLL>
+__device__ __forceinline__ typename Acc<DT, COMP>::T warp_range_sum(const unsigned char* x, int64_t s0, int64_t s1,
+                                                                     int lane) {
+    using A = typename Acc<DT, COMP>::T;
+    constexpr int EB = SegElem<DT>::v;
+    constexpr int PV = VB / EB;
+    constexpr int W = VB / 4;
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x);
+    int64_t a0 = s0 + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0 * EB) % VB) % VB) / EB);
+    if (a0 > s1) a0 = s1;
+    const int64_t nv = (s1 - a0) / PV;
+    const int64_t a1 = a0 + nv * PV;
+    A edge = Op<A>::zero();
+    if (lane < a0 - s0) acc_elem<DT>(edge, x, s0 + lane);
+    if (lane < s1 - a1) acc_elem<DT>(edge, x, a1 + lane);
+    A acc[W];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                a0[j] = s0[j] + (int64_t)((((uintptr_t)VB - (xa + (uintptr_t)s0[j] * EB) % VB) % VB) / EB);
-                if (a0[j] > s1[j]) a0[j] = s1[j];
-                nv[j] = (s1[j] - a0[j]) / PV;
-                const int64_t a1 = a0[j] + nv[j] * PV;
-                edge[j] = Op<A>::zero();  // head [s0, a0) and tail [a1, s1), fewer than PV each
-                if (lane < a0[j] - s0[j]) acc_elem<DT>(edge[j], p.x, s0[j] + lane);
-                if (lane < s1[j] - a1) acc_elem<DT>(edge[j], p.x, a1 + lane);
+    for (int q = 0; q < W; ++q) acc[q] = Op<A>::zero();
+    Levels<A> lv;
+    lv.init();
+    const unsigned char* body = x + a0 * EB;
+    for (int64_t v0 = 0; v0 < nv; v0 += 32 * UNROLL) {
+        uint32_t r[UNROLL][W];
 #pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int64_t v = u * 32 + lane;
-                    if (v < nv[j]) ldg_vec(p.x + (a0[j] + v * PV) * EB, r[j][u]);
-                }
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t v = v0 + u * 32 + lane;
+            if (v < nv) ldg_vec(body + v * VB, r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (v0 + u * 32 + lane < nv) AccVec<DT, A, W>::run(acc, r[u]);
+        lv.template after<UNROLL * AddsPerWord<DT>::v>(acc);
+    }
+    return warp_reduce(Op<A>::add(lv.total(acc), edge));
+}
+
+// The last chunk of segment s to finish: partials [base, base + k) in
+// chunk order (lane-strided, then the warp tree), written to out[s].
+template <class P> __device__ __forceinline__ void combine_chunks_typed(const SegParams& p, const SegQueue& q,
+                                                                        int64_t s, int64_t base, int64_t k, int lane) {
+    P acc = Op<P>::zero();
+    for (int64_t j = lane; j < k; j += 32) acc = Op<P>::add(acc, carry_load<P>(q.part, base + j));
+    acc = warp_reduce(acc);
+    if (lane == 0) {
+        if constexpr (std::is_same<P, double>::value) seg_out_d(p, s, acc);
+        else seg_out(p, s, acc);
+    }
+}
+template <class A> __device__ __forceinline__ void combine_chunks(const SegParams& p, const SegQueue& q, int64_t s,
+                                                                  int64_t base, int64_t k, int lane) {
+    if constexpr (std::is_same<A, long long>::value) {
+        combine_chunks_typed<long long>(p, q, s, base, k, lane);
+    } else {
+        if (p.fp64) combine_chunks_typed<double>(p, q, s, base, k, lane);
+        else combine_chunks_typed<A>(p, q, s, base, k, lane);
+    }
+}
+
+constexpr int kAdaptStreamVB = 32, kAdaptStreamUnroll = 4;  // phase 2: 4 KiB per warp in flight
+
+// Launched cooperatively with at most the resident number of CTAs.  VB and
+// UNROLL shape phase 1's whole-warp segments (as the warp form).
+template <int DT, bool COMP, int VB, int UNROLL>
+__global__ void __launch_bounds__(256, 4) seg_adaptive_kernel(const SegParams p, const SegQueue q) {
+    using A = typename Acc<DT, COMP>::T;
+    constexpr int EB = SegElem<DT>::v;
+    grid_dependency_wait();
+    allow_dependents();
+    if (p.bad != nullptr && __ldcg(p.bad) != 0) return;  // every thread, before any grid barrier
+    cg::grid_group g = cg::this_grid();
+    if (!g.is_valid()) {  // not launched cooperatively: never wait
+        if (threadIdx.x == 0) atomicOr(p.err, kErrNotCooperative);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t Wn = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // queue threshold and chunk size (elements): a queued segment of length L
+    // takes at most L / chunk + 1 <= L / chunk + L / thr chunks, so with both
+    // at least 2 total / capacity the queue cannot overflow
+    const int64_t total = __ldg(p.offsets + p.nseg) - __ldg(p.offsets);
+    const int64_t need = (2 * total + q.cap - 1) / q.cap;
+    int64_t thr = kGroupMaxBytes / EB;
+    if (thr < need) thr = need;
+    int64_t chunk = kAdaptChunkBytes / EB;
+    if (chunk < thr) chunk = thr;
+    chunk = (chunk + 31) / 32 * 32;
+
+    // phase 1: blocks of G consecutive segments, block b to warp b mod Wn
+    int64_t G = (p.nseg + Wn - 1) / Wn;
+    G = G < 1 ? 1 : (G > 32 ? 32 : G);
+    for (int64_t b0 = w * G; b0 < p.nseg; b0 += Wn * G)
+        seg_warp_block<DT, COMP, VB, UNROLL, true>(p, &q, b0, (p.nseg - b0 < G) ? p.nseg - b0 : G, lane, thr, chunk);
+
+    g.sync();  // every long segment's chunks are queued
+
+    // phase 2: chunks from the queue
+    const int64_t nq = min((int64_t)__ldcg(q.ctr), q.cap);
+    unsigned idx = 0;
+    if (lane == 0) idx = atomicAdd(q.ctr + 1, 1u);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    // the current chunk's descriptor and offsets are read one chunk ahead:
+    // lane 0 holds (segment, j | k, segment start, end) of the next chunk
+    int64_t ds = 0, de = 0;
+    long long djk = 0, dsg = 0;
+    if (lane == 0 && (int64_t)idx < nq) {
+        dsg = __ldcg(q.desc + 2 * (int64_t)idx);
+        djk = __ldcg(q.desc + 2 * (int64_t)idx + 1);
+        ds = __ldg(p.offsets + dsg);
+        de = __ldg(p.offsets + dsg + 1);
+    }
+    while ((int64_t)idx < nq) {
+        const int64_t s = __shfl_sync(0xffffffffu, dsg, 0);
+        const long long jk = __shfl_sync(0xffffffffu, djk, 0);
+        const int64_t o = __shfl_sync(0xffffffffu, ds, 0), e = __shfl_sync(0xffffffffu, de, 0);
+        const int64_t j = jk >> 32, k = jk & 0xffffffffll;
+        unsigned nxt = 0;
+        if (lane == 0) {  // the next chunk and its descriptor, while this one is summed
+            nxt = atomicAdd(q.ctr + 1, 1u);
+            if ((int64_t)nxt < nq) {
+                dsg = __ldcg(q.desc + 2 * (int64_t)nxt);
+                djk = __ldcg(q.desc + 2 * (int64_t)nxt + 1);
+                ds = __ldg(p.offsets + dsg);
+                de = __ldg(p.offsets + dsg + 1);
             }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-#pragma unroll
-                for (int q = 0; q < W; ++q) acc[j][q] = Op<A>::zero();
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    if (u * 32 + lane < nv[j]) {
-#pragma unroll
-                        for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[j][u][q]);
-                    }
-                }
-            }
-            // the rest of a segment longer than one batch, with both batch
-            // buffers free now: 2 * UNROLL vectors per lane in flight
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const unsigned char* body = p.x + a0[j] * EB;
-                for (int64_t v0 = 32 * UNROLL; v0 < nv[j]; v0 += 64 * UNROLL) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                        for (int u = 0; u < UNROLL; ++u) {
-                            const int64_t v = v0 + (h * UNROLL + u) * 32 + lane;
-                            if (v < nv[j]) ldg_vec(body + v * VB, r[h][u]);
-                        }
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                        for (int u = 0; u < UNROLL; ++u) {
-                            if (v0 + (h * UNROLL + u) * 32 + lane < nv[j]) {
-#pragma unroll
-                                for (int q = 0; q < W; ++q) acc_word<DT>(acc[j][q], r[h][u][q]);
-                            }
-                        }
-                    }
-                }
-            }
-            const A t0 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[0]), edge[0]));
-            const A t1 = warp_reduce(Op<A>::add(sum_words<A, W>(acc[1]), edge[1]));
-            if (lane == 0) {
-                seg_out(p, b0 + k0, t0);
-                if (two) seg_out(p, b0 + k1, t1);
-            }
+        }
+        const int64_t c0 = o + j * chunk;
+        const int64_t c1 = c0 + chunk < e ? c0 + chunk : e;
+        const A v = warp_range_sum<DT, COMP, kAdaptStreamVB, kAdaptStreamUnroll>(p.x, c0, c1, lane);
+        const int64_t base = (int64_t)idx - j;
+        if (k == 1) {  // a segment of one chunk: no partial, no ticket
+            if (lane == 0) seg_out(p, s, v);
+            idx = __shfl_sync(0xffffffffu, nxt, 0);
+            continue;
+        }
+        unsigned t = 0;
+        if (lane == 0) {
+            carry_store(p, q.part, (int64_t)idx, v);
+            __threadfence();
+            t = atomicAdd(q.tick + base, 1u);
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int64_t)t == k - 1) {  // the segment's last chunk: combine in chunk order
+            __threadfence();
+            combine_chunks<A>(p, q, s, base, k, lane);
+        }
+        idx = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    // the last warp out resets the counters for the next launch
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(q.ctr + 2, 1u) == (unsigned)(Wn - 1)) {
+            q.ctr[0] = 0u;
+            q.ctr[1] = 0u;
+            q.ctr[2] = 0u;
+            __threadfence();
         }
     }
 }
 
+// Phase 1 runs the warp form's default shape (16-byte vectors, 2 per lane).
+template <int DT, bool COMP>
+inline const void* pick_seg_adapt(int vec, int unroll) {
+    return (vec == 16 && unroll == 2) ? (const void*)seg_adaptive_kernel<DT, COMP, 16, 2> : nullptr;
+}
 
 template <int DT, bool COMP, int VB>
 inline const void* pick_seg_warp_u(int unroll) {

@@ -318,6 +318,7 @@ WARP = 0x4000  # SR_F_WARPSEGMENTS: whole segments per warp, no grid stage
 
 
 LANE = 0x8000  # SR_F_LANE_SEGMENTS: whole segments per thread, no grid stage
+ADAPT = 0x10000  # SR_F_ADAPTIVE_SEGMENTS: lanes / warps / queued chunks, one cooperative launch
 
 
 @pytest.mark.parametrize("form,vec,unroll,block", [
@@ -404,7 +405,7 @@ def test_warp_segments_plan_and_determinism(sr):
 
 
 @pytest.mark.parametrize("stage", STAGES)
-@pytest.mark.parametrize("flags", [0, BULK, WARP, LANE])
+@pytest.mark.parametrize("flags", [0, BULK, WARP, LANE, ADAPT])
 def test_checked_entry(sr, stage, flags):
     """sr_reduce_sum_segmented_checked: valid offsets give the oracle's sums;
     offsets past the declared element count, a decreasing pair or a negative
@@ -441,6 +442,133 @@ def test_checked_entry(sr, stage, flags):
     for bad in (past, swapped, negative):
         st, got = run(bad)
         assert st == sr.ERR_ARG
-        assert np.all(got == (0 if stage == sr.ATOMIC and not flags & (WARP | LANE) else -7))   # nothing summed
+        assert np.all(got == (0 if stage == sr.ATOMIC and not flags & (WARP | LANE | ADAPT) else -7))  # nothing summed
     st, got = run(good)
     assert st == sr.OK and np.array_equal(got, oracle.segsum_i32(x, good))
+
+
+# ---------------------------------------------------------------- adaptive form
+@pytest.mark.parametrize("nseg,max_len", [(1, 0), (1, 1), (1, 100_000), (2, 5), (31, 0), (33, 7),
+                                          (500, 300), (5000, 40), (300, 20_000), (40, 200_000)])
+def test_adaptive_random_layouts(sr, nseg, max_len):
+    """Random layouts through all three paths (segments of up to 512 bytes
+    by lanes, up to one 16,384-element chunk by warps, longer ones queued as
+    chunks), grids of one CTA up to the resident maximum, misaligned input."""
+    off = workloads.random_segment_offsets(nseg, max_len, seed=nseg + max_len + 7)
+    n = int(off[-1])
+    xf = workloads.uniform_f32(n, seed=11)
+    xi = workloads.uniform_i32(n, seed=11)
+    for grid in (0, 1, 3):
+        for x_off in (0, 1, 3):
+            _check(sr, xi, off, ADAPT, x_off, grid=grid)
+            _check(sr, xf, off, ADAPT, x_off, grid=grid)
+
+
+@pytest.mark.parametrize("median,sigma,hi", [(40, 1.5, 1 << 16), (512, 2.5, 1 << 22), (4096, 1.94, 1 << 24)])
+def test_adaptive_skewed_layouts(sr, median, sigma, hi):
+    """Lognormal layouts with long tails (empty segments included): short,
+    mid-length and multi-chunk segments in one call; int32 exact, binary32
+    within the gate; the same result on every call (deterministic)."""
+    n_total = 1 << 22
+    nseg = max(1, n_total // (median * 2))
+    off = workloads.segment_offsets(nseg, n_total, seed=median, median=median, sigma=sigma, lo=0, hi=hi)
+    n = int(off[-1])
+    xi = workloads.uniform_i32(n, seed=12)
+    xf = workloads.uniform_f32(n, seed=12)
+    _check(sr, xi, off, ADAPT)
+    got = _check(sr, xf, off, ADAPT, 1)
+    for _ in range(3):
+        assert np.array_equal(_check(sr, xf, off, ADAPT, 1), got)
+
+
+@pytest.mark.parametrize("flags", [0x100, 0x300, 0x200])
+def test_adaptive_precision_flags(sr, flags):
+    off = workloads.segment_offsets(600, 1 << 22, seed=13, median=1024, sigma=2.5, hi=1 << 21)
+    x = workloads.lognormal_f32(int(off[-1]), seed=13, sigma=3.0)
+    _check(sr, x, off, ADAPT | flags)
+
+
+def test_adaptive_bf16_and_fp8(sr):
+    off = workloads.segment_offsets(400, 1 << 21, seed=14, median=256, sigma=2.5, hi=1 << 20)
+    n = int(off[-1])
+    x = workloads.lognormal_f32(n, seed=14, sigma=2.0)
+    bits = workloads.to_bf16_bits(x)
+    codes, deq = workloads.to_e4m3_codes(x)
+    od = torch.from_numpy(off).cuda()
+    dec_b = np.frombuffer((bits.astype(np.uint32) << 16).tobytes(), dtype=np.float32)
+    xd_b = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    got = sr.reduce_sum_segmented(xd_b, od, variant=ADAPT).cpu().numpy()
+    ex = oracle.segexact_f32(dec_b, off)
+    assert np.all(np.abs(got - ex) <= 4 * EPS32 * oracle.segsum_abs_f32(dec_b, off) + 1e-30)
+    dec_f = (torch.from_numpy(codes).view(torch.float8_e4m3fn).float() * deq).numpy()
+    got = sr.reduce_sum_segmented(torch.from_numpy(codes).cuda(), od,
+                                  config=sr.make_config(ADAPT, scale=deq)).cpu().numpy()
+    for s in range(400):
+        a, b = off[s], off[s + 1]
+        exs = oracle.to_float(oracle.exact_e4m3(codes[a:b], deq))
+        sabs = float(np.abs(dec_f[a:b]).astype(np.float64).sum())
+        assert abs(got[s] - exs) <= 4 * EPS32 * sabs * 1.001 + 1e-30, s
+
+
+def test_adaptive_leaves_the_workspace_clean(sr):
+    """The chunk queue lives in the stream's segmented workspace beside the
+    flat split's tickets: after adaptive calls, last-block-done flat-split
+    calls on the same stream (which need those tickets at zero) stay exact,
+    and so does the next adaptive call."""
+    off = workloads.segment_offsets(2000, 1 << 22, seed=15, median=2048, sigma=2.0, hi=1 << 20)
+    x = workloads.uniform_i32(int(off[-1]), seed=15)
+    for v in (ADAPT, 3, ADAPT, 3, 3 | BULK, ADAPT):
+        _check(sr, x, off, v)
+    assert sr.stream_status() == sr.OK
+
+
+def test_adaptive_in_a_graph(sr):
+    off = workloads.segment_offsets(3000, 1 << 22, seed=17, median=512, sigma=2.5, hi=1 << 20)
+    x = workloads.uniform_f32(int(off[-1]), seed=17)
+    xd, od = _dev(x), torch.from_numpy(off).cuda()
+    out = torch.empty(3000, dtype=torch.float32, device="cuda")
+    ref = sr.reduce_sum_segmented(xd, od, variant=ADAPT).cpu().numpy()
+    g = sr.SegmentedGraph(xd, od, out, sr.make_config(ADAPT))
+    for _ in range(3):
+        out.fill_(-1)
+        g.launch()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
+    g.close()
+    assert sr.stream_status() == sr.OK
+
+
+def test_adaptive_refusals(sr):
+    x = torch.zeros(64, dtype=torch.float32, device="cuda")
+    od = torch.tensor([0, 32, 64], dtype=torch.int64, device="cuda")
+    out = torch.empty(2, dtype=torch.float32, device="cuda")
+    props = torch.cuda.get_device_properties(0)
+    for kw, want in (({"vec_bytes": 32}, sr.ERR_UNSUPPORTED), ({"unroll": 4}, sr.ERR_UNSUPPORTED),
+                     ({"block_threads": 128}, sr.ERR_UNSUPPORTED),
+                     ({"grid": props.multi_processor_count * 40}, sr.ERR_LAUNCH)):  # valid, not co-resident
+        st = sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), 2, sr.F32, out.data_ptr(),
+                                         sr.make_config(ADAPT, **kw))
+        assert st == want, kw
+    for other in (BULK, WARP, LANE, DENSE):
+        st = sr.reduce_sum_segmented_ptr(x.data_ptr(), od.data_ptr(), 2, sr.F32, out.data_ptr(),
+                                         sr.make_config(ADAPT | other))
+        assert st == sr.ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_adaptive_largest_queue(sr):
+    """2^30 int32 values in ~32,000 segments of 16,385 to 50,000 elements:
+    the chunk size grows past 16,384 elements (2 x 2^30 / 98,304 = 21,846)
+    and the queue fills to ~80 % of its capacity; exact per segment."""
+    rng = np.random.default_rng(18)
+    lens = rng.integers(16_385, 50_001, 40_000)
+    lens = lens[np.cumsum(lens) <= (1 << 30)]
+    off = np.zeros(lens.size + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    n = int(off[-1])
+    xd = torch.randint(-1000, 1001, (n,), dtype=torch.int32, device="cuda")
+    od = torch.from_numpy(off).cuda()
+    got = sr.reduce_sum_segmented(xd, od, variant=ADAPT).cpu().numpy()
+    x = xd.cpu().numpy()
+    assert np.array_equal(got, oracle.segsum_i32(x, off))
+    assert sr.stream_status() == sr.OK
