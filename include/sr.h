@@ -503,7 +503,10 @@ int sr_selector_choose(sr_selector selector, int64_t n, int dtype, int64_t nseg,
  * SR_F_DENSE_SEGMENTS to the chosen configuration, or replaces the chosen
  * configuration's shape with SR_F_WARP_SEGMENTS or SR_F_LANE_SEGMENTS at its
  * default shape (the lane form with 32-byte vectors from 128 bytes per
- * segment on average). */
+ * segment on average).  This layout rule runs after the selector (or the
+ * autotuner) and overrides its shape: the selector's candidates, and so its
+ * regret against exhaustive autotuning, cover the grid stage, grid size and
+ * vector width of the plain and dense forms only. */
 int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int dtype, void* out,
                            sr_stream_t stream);
 /* The segmented form for a layout, from the caller's segment-length
@@ -518,6 +521,13 @@ int sr_reduce_sum_selected(sr_selector selector, const void* x, int64_t n, int d
  * segments (<= 512 bytes, std <= mean / 2); else 0 (the plain form).
  * Host-only and pure (no device call).  The paper has no counterpart: the
  * thresholds come from this library's own measurements of the forms.
+ * The statistics must describe the layout actually passed: they are trusted,
+ * not checked against the offsets.  A len_max below the true longest segment
+ * can route a layout with a very long segment to the lane or warp form, where
+ * one thread or one warp sums that segment alone (still correct, but up to
+ * hundreds of times slower than the plain form).  Callers without reliable
+ * statistics should use SR_F_ADAPTIVE_SEGMENTS, which partitions the segments
+ * from the offsets on the device.
  * Returns the flag, or a negated status: -SR_ERR_DTYPE, -SR_ERR_ARG (sms < 1,
  * nseg < 0, negative or NaN statistics). */
 int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean, double len_std, double len_max);
