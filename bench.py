@@ -160,7 +160,37 @@ def cpu_baseline(seconds=10.0):
     return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": "%d passes of the sequential FP64 loop over the first 2^25 elements (128 MiB) of the "
                       "same U[-1,1] seed-0 workload, %.1f s" % (reps, el),
-            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+            "cpu": _cpu_model(), "host_cores": os.cpu_count(),
+            "parallel": cpu_baseline_parallel(x, seconds / 2)}
+
+
+def cpu_baseline_parallel(x, seconds):
+    """The same oracle loop on every host core: the sample cut into one
+    contiguous slice per thread (the C loop runs without the interpreter lock),
+    the slices' FP64 partials added in slice order."""
+    import concurrent.futures as cf
+    import numpy as np
+    import oracle
+    T = max(1, os.cpu_count() or 1)
+    n = x.size
+    cuts = [n * i // T for i in range(T + 1)]
+    parts = [x[cuts[i]:cuts[i + 1]] for i in range(T)]
+    with cf.ThreadPoolExecutor(max_workers=T) as ex:
+        def one_pass():
+            return float(np.sum(np.array(list(ex.map(oracle.sum_f32, parts)), dtype=np.float64)))
+        s_par = one_pass()
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            one_pass()
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    s_seq = oracle.sum_f32(x)
+    return {"value": round(reps * n * 4 / el / 1e9, 3), "unit": "GB/s", "cores": T,
+            "sample": "%d passes over the same 2^25 elements, %d threads each running the sequential FP64 loop "
+                      "on one contiguous slice, partials added in order, %.1f s" % (reps, T, el),
+            "rel_diff_vs_sequential": abs(s_par - s_seq) / max(abs(s_seq), 1e-300)}
 
 
 def _cpu_model():

@@ -219,7 +219,11 @@ typedef struct {
  * aligned to the element size.  out: device scalar — int64 for SR_I32, float
  * otherwise, double when SR_F_FP64_COMBINE is set.  n == 0 writes 0.
  * Errors: SR_ERR_ARG (n < 0, NULL x with n > 0, NULL out, misaligned x or out),
- * SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA. */
+ * SR_ERR_DTYPE, SR_ERR_LAUNCH, SR_ERR_UNSUPPORTED, SR_ERR_CUDA.
+ * variant SR_AUTO leaves the choice to the library: SR_AUTO's own rule, or the
+ * variant the environment variable SR_VARIANT names (sr_parse_variant's
+ * syntax, read once per process; one that does not parse makes these calls
+ * return SR_ERR_ARG). */
 int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant,
                   sr_stream_t stream);
 
@@ -240,7 +244,9 @@ int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant,
 int sr_reduce_sum_host(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg,
                        sr_stream_t stream);
 
-/* Same with an explicit launch configuration (NULL cfg = defaults). */
+/* Same with an explicit launch configuration (NULL cfg = the library's
+ * choice: SR_AUTO, or the variant SR_VARIANT names as for sr_reduce_sum; a
+ * configuration passed in is used as given, SR_VARIANT set or not). */
 int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out,
                      const sr_config* cfg, sr_stream_t stream);
 
@@ -264,7 +270,8 @@ int sr_stream_release(sr_stream_t stream);
  * current device, without launching: fills *resolved (variant with the
  * stage, cluster and load path chosen, block_threads, grid, vec_bytes,
  * unroll, tile_bytes, stages).
- * Needs a device; returns the same errors sr_reduce_sum_ex would. */
+ * Needs a device; returns the same errors sr_reduce_sum_ex would.  cfg ==
+ * NULL plans the library's choice (SR_VARIANT when set, as sr_reduce_sum_ex). */
 int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
 
 /* ------------------------------------------------------ segmented sum */
@@ -534,6 +541,62 @@ int sr_segmented_layout_flags(int sms, int dtype, int64_t nseg, double len_mean,
 int sr_reduce_sum_segmented_selected(sr_selector selector, const void* x, const int64_t* offsets, int64_t nseg,
                                      int dtype, void* out, double len_mean, double len_std, double len_max,
                                      sr_stream_t stream);
+
+/* --------------------------------- persisted selection and configuration */
+
+/* Reads a variant from text: a decimal or 0x-hexadecimal number, or names
+ * joined by '+': at most one grid stage (auto, two_kernel, atomic,
+ * last_block, grid_sync, single_cluster), at most one cluster size (cluster2,
+ * cluster4, cluster8, cluster16) and the flags kahan, fp64_combine,
+ * fp64_auto, bulk, each at most once — e.g. "last_block+bulk" = 0x403.
+ * Surrounding blanks are ignored.  Host-only and pure.  Only the syntax is
+ * checked here; a call validates the combination as for any variant.
+ * Errors: SR_ERR_ARG (NULL argument, empty text, unknown name, repeated
+ * stage, cluster or flag, number out of range). */
+int sr_parse_variant(const char* text, int* variant);
+
+/* The autotuner fallback of sr_reduce_sum_selected /
+ * sr_reduce_sum_segmented_selected memoises its choice per device identity
+ * and call shape (n, dtype, segment count, segment statistics at 1/16-octave
+ * resolution).  The memo can be kept across processes in a versioned text
+ * file ("sr-tune 1"): sections headed "device <SMs> <driver version>
+ * <name>", one line per shape.  A device's identity is its name, its SM count
+ * and the CUDA driver version (cudaDriverGetVersion): entries are used only
+ * on a device with the same identity and carried along otherwise.
+ * When the environment variable SR_TUNE_FILE names a file, the memo is read
+ * from it at its first use (a missing file is created at the first new
+ * entry; a file that does not parse is neither used nor overwritten) and the
+ * file is rewritten, whole, after every new entry.  Files are written to a
+ * temporary name and renamed, so a reader never sees a partial file; of
+ * concurrent writers the last rename wins.  Host-only; no device call.
+ * sr_tune_save: writes the memo (every identity) to `path`.
+ * sr_tune_load: merges the entries of `path` into the memo (an entry of the
+ *   file replaces one with the same key); *entries (may be NULL) = entries
+ *   read.  The whole file is parsed first: a malformed file (SR_ERR_ARG)
+ *   changes nothing.
+ * sr_tune_size: entries in the memo; sr_tune_clear: empties it.
+ * Errors: SR_ERR_ARG (NULL or empty path, unreadable, unwritable or
+ * malformed file). */
+int sr_tune_save(const char* path);
+int sr_tune_load(const char* path, int64_t* entries);
+int64_t sr_tune_size(void);
+int sr_tune_clear(void);
+
+/* A trained selector (its MLP's dimensions and parameters, the feature
+ * normalisation and the candidate list) as a versioned text file
+ * ("sr-selector 1"), stamped with the identity of the device it was saved on.
+ * sr_selector_save: writes `selector` to `path` (needs the current device for
+ *   its identity).
+ * sr_selector_load: reads `path` and creates a selector for the current
+ *   device that owns its own MLP (sr_selector_destroy frees both).  The file
+ *   is parsed before any device call: malformed -> SR_ERR_ARG; made on a
+ *   device with another identity -> SR_ERR_UNSUPPORTED.
+ * When the environment variable SR_MODEL_FILE names a selector file, the
+ * selected entry points called with selector == NULL use the selector loaded
+ * from it (once per device, kept until the process exits) instead of the
+ * autotuner; if that load fails they return its status. */
+int sr_selector_save(sr_selector selector, const char* path);
+int sr_selector_load(const char* path, sr_selector* selector);
 
 /* ------------------------------------------------- allocation-free sum */
 

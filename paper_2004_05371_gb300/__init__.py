@@ -184,6 +184,20 @@ def load():
     L.sr_stream_status.argtypes = [vp]
     L.sr_plan.restype = i32
     L.sr_plan.argtypes = [i64, i32, ctypes.POINTER(Config), ctypes.POINTER(Config)]
+    L.sr_parse_variant.restype = i32
+    L.sr_parse_variant.argtypes = [ctypes.c_char_p, ctypes.POINTER(i32)]
+    L.sr_tune_save.restype = i32
+    L.sr_tune_save.argtypes = [ctypes.c_char_p]
+    L.sr_tune_load.restype = i32
+    L.sr_tune_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
+    L.sr_tune_size.restype = i64
+    L.sr_tune_size.argtypes = []
+    L.sr_tune_clear.restype = i32
+    L.sr_tune_clear.argtypes = []
+    L.sr_selector_save.restype = i32
+    L.sr_selector_save.argtypes = [vp, ctypes.c_char_p]
+    L.sr_selector_load.restype = i32
+    L.sr_selector_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
     L.sr_status_string.restype = ctypes.c_char_p
     L.sr_status_string.argtypes = [i32]
     L.sr_last_cuda_error.restype = i32
@@ -476,6 +490,18 @@ class NativeSelector:
         check(lib().sr_selector_create(mlp.h, self._mu, self._sd, cands, len(cands), ctypes.byref(self.h)),
               "sr_selector_create")
 
+    @classmethod
+    def load(cls, path):
+        """A selector from a file written by save(); it owns its own MLP."""
+        self = cls.__new__(cls)
+        self.mlp, self.cands = None, None
+        self.h = ctypes.c_void_p()
+        check(lib().sr_selector_load(os.fsencode(path), ctypes.byref(self.h)), "sr_selector_load")
+        return self
+
+    def save(self, path):
+        check(lib().sr_selector_save(self.h, os.fsencode(path)), "sr_selector_save")
+
     def choose(self, n, dtype, nseg=1, mean=None, std=0.0, mx=None, stream=None) -> Config:
         c = Config()
         mean = float(n) if mean is None else mean
@@ -494,6 +520,30 @@ class NativeSelector:
             self.close()
         except Exception:
             pass
+
+
+def parse_variant(text: str) -> int:
+    v = ctypes.c_int(0)
+    check(lib().sr_parse_variant(text.encode(), ctypes.byref(v)), "sr_parse_variant(%r)" % text)
+    return v.value
+
+
+def tune_save(path):
+    check(lib().sr_tune_save(os.fsencode(path)), "sr_tune_save")
+
+
+def tune_load(path) -> int:
+    k = ctypes.c_int64(0)
+    check(lib().sr_tune_load(os.fsencode(path), ctypes.byref(k)), "sr_tune_load")
+    return k.value
+
+
+def tune_size() -> int:
+    return int(lib().sr_tune_size())
+
+
+def tune_clear():
+    check(lib().sr_tune_clear(), "sr_tune_clear")
 
 
 def reduce_sum_selected_ptr(selector, x_ptr, n, dtype, out_ptr, stream=None) -> int:

@@ -198,13 +198,29 @@ sr_config default_config(int variant) {
     c.variant = variant;
     return c;
 }
+
+// The configuration of a single-array sum: the caller's, or — cfg == NULL,
+// the library's choice — SR_AUTO unless SR_VARIANT names a variant.
+int library_choice(const sr_config* cfg, sr_config* c) {
+    if (cfg) {
+        *c = *cfg;
+        return SR_OK;
+    }
+    int v = SR_AUTO;
+    const int st = env_variant(&v);
+    if (st != SR_OK) return st;
+    *c = default_config(v);
+    return SR_OK;
+}
 }  // namespace
 
 extern "C" {
 
 int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out, const sr_config* cfg, sr_stream_t stream) {
-    const sr_config c = cfg ? *cfg : default_config(SR_AUTO);
-    int st = reduce_validate(x, n, dtype, out, c);
+    sr_config c;
+    int st = library_choice(cfg, &c);
+    if (st != SR_OK) return st;
+    st = reduce_validate(x, n, dtype, out, c);
     if (st != SR_OK) return st;
     const DeviceInfo* d = current_device(&st);
     if (!d) return st;
@@ -218,6 +234,7 @@ int sr_reduce_sum_ex(const void* x, int64_t n, int dtype, void* out, const sr_co
 }
 
 int sr_reduce_sum(const void* x, int64_t n, int dtype, void* out, int variant, sr_stream_t stream) {
+    if (variant == SR_AUTO) return sr_reduce_sum_ex(x, n, dtype, out, nullptr, stream);
     const sr_config c = default_config(variant);
     return sr_reduce_sum_ex(x, n, dtype, out, &c, stream);
 }
@@ -355,7 +372,9 @@ int sr_graph_destroy(sr_graph g) {
 
 int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved) {
     if (!resolved) return SR_ERR_ARG;
-    const sr_config c = cfg ? *cfg : default_config(SR_AUTO);
+    sr_config c;
+    int st0 = library_choice(cfg, &c);
+    if (st0 != SR_OK) return st0;
     // A 256-byte-aligned stand-in address: plans assume an aligned array.
     const void* fake = reinterpret_cast<const void*>(uintptr_t(1) << 20);
     int st = reduce_validate(fake, n, dtype, fake, c);

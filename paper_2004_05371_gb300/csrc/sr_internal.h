@@ -4,6 +4,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/sr.h"
@@ -94,6 +96,28 @@ inline int elem_size(int dtype) { return dtype == SR_BF16 ? 2 : (dtype == SR_FP8
 // the stream's previous work (sr_reduce.cu).  Used where the atomic finish
 // needs a zeroed output: a memset node costs several microseconds more.
 int launch_zero(void* p, size_t bytes, cudaStream_t s);
+
+// Configuration and persisted selection state (sr_persist.cu)
+// The identity a device's persisted entries are keyed by: "<SMs> <driver
+// version> <name>" (cached per device ordinal).
+int device_identity(int dev, std::string* id);
+// The autotuner fallback's memo, shared by every selected entry point.
+int tune_lookup(int dev, int64_t n, int dtype, int64_t nseg, double mean, double sd, double mx, sr_config* cfg,
+                bool* found);
+int tune_insert(int dev, int64_t n, int dtype, int64_t nseg, double mean, double sd, double mx,
+                const sr_config& cfg);
+// The variant SR_VARIANT names (SR_AUTO when unset); SR_ERR_ARG when it does not parse.
+int env_variant(int* variant);
+// A trained selector as stored in its text file.
+struct SelectorFile {
+    std::string ident;  // device_identity() of the GPU it was trained on
+    int din = 0, dh = 0, dout = 0;
+    float mu[SR_SELECTOR_FEATURES] = {}, sd[SR_SELECTOR_FEATURES] = {};
+    std::vector<sr_config> cands;
+    std::vector<float> params;
+};
+int read_selector_file(const char* path, SelectorFile* f);  // SR_ERR_ARG: unreadable or malformed
+int write_selector_file(const char* path, const SelectorFile& f);
 
 // Single-array reduction (sr_reduce.cu)
 int reduce_validate(const void* x, int64_t n, int dtype, const void* out, const sr_config& cfg);

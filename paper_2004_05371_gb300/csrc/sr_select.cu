@@ -1,7 +1,10 @@
 // Per-call launch selection: a trained MLP (served by its inference kernel)
 // or, without one, exhaustive autotuning on the call's own data — both
-// memoised per call shape, so a shape pays the choice once.
+// memoised per call shape, so a shape pays the choice once.  Selectors are
+// saved to and loaded from text files; SR_MODEL_FILE names one that calls
+// made without a selector use instead of the autotuner.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -21,9 +24,6 @@ ShapeKey make_key(int dev, int64_t n, int dtype, int64_t nseg, double mean, doub
     return ShapeKey(dev, n, dtype, nseg, q(mean), q(sd), q(mx));
 }
 
-std::mutex g_tune_mu;
-std::map<ShapeKey, sr_config> g_tuned;  // autotuner fallback memo
-
 int current_dev(int* dev) {
     cudaError_t e = cudaGetDevice(dev);
     return e == cudaSuccess ? SR_OK : status_from_cuda(e);
@@ -32,10 +32,38 @@ int current_dev(int* dev) {
 }  // namespace
 }  // namespace sr
 
+namespace {
+// Per device: the selector SR_MODEL_FILE names, loaded at its first use
+// (status, selector); kept until the process exits.
+std::mutex g_env_sel_mu;
+std::map<int, std::pair<int, sr_selector>> g_env_sel;
+
+// The selector of a call made without one: SR_MODEL_FILE's when the
+// variable is set (its load status otherwise), else none (the autotuner).
+int env_selector(sr_selector* s) {
+    *s = nullptr;
+    const char* path = std::getenv("SR_MODEL_FILE");
+    if (!path || !*path) return SR_OK;
+    int dev = 0;
+    int st = sr::current_dev(&dev);
+    if (st != SR_OK) return st;
+    std::lock_guard<std::mutex> lk(g_env_sel_mu);
+    auto it = g_env_sel.find(dev);
+    if (it == g_env_sel.end()) {
+        sr_selector sel = nullptr;
+        const int ls = sr_selector_load(path, &sel);
+        it = g_env_sel.emplace(dev, std::make_pair(ls, sel)).first;
+    }
+    *s = it->second.second;
+    return it->second.first;
+}
+}  // namespace
+
 using namespace sr;
 
 struct sr_selector_s {
     sr_mlp mlp = nullptr;
+    bool owns_mlp = false;  // made by sr_selector_load
     float mu[SR_SELECTOR_FEATURES];
     float sd[SR_SELECTOR_FEATURES];
     std::vector<sr_config> cands;
@@ -75,7 +103,56 @@ int sr_selector_destroy(sr_selector s) {
     if (!s) return SR_OK;
     cudaFree(s->d_x);
     cudaFree(s->d_cls);
-    delete s;  // the MLP stays owned by the caller
+    if (s->owns_mlp) sr_mlp_destroy(s->mlp);  // otherwise the MLP stays owned by the caller
+    delete s;
+    return SR_OK;
+}
+
+int sr_selector_save(sr_selector s, const char* path) {
+    if (!s || !path || !*path) return SR_ERR_ARG;
+    int dev = 0;
+    int st = current_dev(&dev);
+    if (st != SR_OK) return st;
+    SelectorFile f;
+    st = device_identity(dev, &f.ident);
+    if (st != SR_OK) return st;
+    st = sr_mlp_dims(s->mlp, &f.din, &f.dh, &f.dout);
+    if (st != SR_OK) return st;
+    std::memcpy(f.mu, s->mu, sizeof f.mu);
+    std::memcpy(f.sd, s->sd, sizeof f.sd);
+    f.cands = s->cands;
+    f.params.resize((size_t)sr_mlp_param_count(s->mlp));
+    st = sr_mlp_get_params(s->mlp, f.params.data(), (int64_t)f.params.size());
+    if (st != SR_OK) return st;
+    return write_selector_file(path, f);
+}
+
+int sr_selector_load(const char* path, sr_selector* out) {
+    if (!out) return SR_ERR_ARG;
+    *out = nullptr;
+    SelectorFile f;
+    int st = read_selector_file(path, &f);  // the whole file parses before any device call
+    if (st != SR_OK) return st;
+    int dev = 0;
+    st = current_dev(&dev);
+    if (st != SR_OK) return st;
+    std::string id;
+    st = device_identity(dev, &id);
+    if (st != SR_OK) return st;
+    if (id != f.ident) return SR_ERR_UNSUPPORTED;  // trained on another GPU model or driver
+    sr_mlp m = nullptr;
+    st = sr_mlp_create(f.din, f.dh, f.dout, &m);
+    if (st != SR_OK) return st;
+    if (sr_mlp_param_count(m) != (int64_t)f.params.size()) st = SR_ERR_ARG;
+    if (st == SR_OK) st = sr_mlp_set_params(m, f.params.data(), (int64_t)f.params.size());
+    sr_selector s = nullptr;
+    if (st == SR_OK) st = sr_selector_create(m, f.mu, f.sd, f.cands.data(), (int)f.cands.size(), &s);
+    if (st != SR_OK) {
+        sr_mlp_destroy(m);
+        return st;
+    }
+    s->owns_mlp = true;
+    *out = s;
     return SR_OK;
 }
 
@@ -122,15 +199,9 @@ static int tuned_config(const void* x, int64_t n, const int64_t* offsets, int64_
     int dev = 0;
     int st = current_dev(&dev);
     if (st != SR_OK) return st;
-    const ShapeKey key = make_key(dev, n, dtype, nseg, mean, sd, mx);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) {
-            *cfg = it->second;
-            return SR_OK;
-        }
-    }
+    bool found = false;
+    st = tune_lookup(dev, n, dtype, nseg, mean, sd, mx, cfg, &found);
+    if (st != SR_OK || found) return st;
     const DeviceInfo* d = current_device(&st);
     if (!d) return st;
     const int nc = sr_candidates(0, d->sms, nullptr, 0);
@@ -143,20 +214,18 @@ static int tuned_config(const void* x, int64_t n, const int64_t* offsets, int64_
     for (int i = 1; i < nc; ++i)
         if (us[i] < us[best]) best = i;
     if (!std::isfinite(us[best])) return SR_ERR_LAUNCH;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = c[best];
-    }
     *cfg = c[best];
-    return SR_OK;
+    return tune_insert(dev, n, dtype, nseg, mean, sd, mx, c[best]);
 }
 
 int sr_reduce_sum_selected(sr_selector s, const void* x, int64_t n, int dtype, void* out, sr_stream_t stream) {
     if (n < 0) return SR_ERR_ARG;
     sr_config c;
     const double dn = (double)n;
-    int st = s ? sr_selector_choose(s, n, dtype, 1, dn, 0.0, dn, &c, stream)
-               : tuned_config(x, n, nullptr, 1, dtype, out, dn, 0.0, dn, &c, stream);
+    int st = s ? SR_OK : env_selector(&s);
+    if (st != SR_OK) return st;
+    st = s ? sr_selector_choose(s, n, dtype, 1, dn, 0.0, dn, &c, stream)
+           : tuned_config(x, n, nullptr, 1, dtype, out, dn, 0.0, dn, &c, stream);
     if (st != SR_OK) return st;
     return sr_reduce_sum_ex(x, n, dtype, out, &c, stream);
 }
@@ -167,8 +236,10 @@ int sr_reduce_sum_segmented_selected(sr_selector s, const void* x, const int64_t
     if (nseg < 1) return nseg == 0 ? SR_OK : SR_ERR_ARG;
     const int64_t n = (int64_t)std::llround(len_mean * (double)nseg);
     sr_config c;
-    int st = s ? sr_selector_choose(s, n, dtype, nseg, len_mean, len_std, len_max, &c, stream)
-               : tuned_config(x, n, offsets, nseg, dtype, out, len_mean, len_std, len_max, &c, stream);
+    int st = s ? SR_OK : env_selector(&s);
+    if (st != SR_OK) return st;
+    st = s ? sr_selector_choose(s, n, dtype, nseg, len_mean, len_std, len_max, &c, stream)
+           : tuned_config(x, n, offsets, nseg, dtype, out, len_mean, len_std, len_max, &c, stream);
     if (st != SR_OK) return st;
     const sr::DeviceInfo* d = sr::current_device(&st);
     if (!d) return st;
