@@ -254,9 +254,9 @@ def main():
                     help="secondary measurement suites (JSON lines); the default run is the headline")
     ap.add_argument("--layout", default=None,
                     help="seglayouts suite: only the layouts whose name contains this text (profiling runs)")
-    ap.add_argument("--seg-form", default=None, choices=["ldg256", "dense256", "ldg512", "dense512", "tma", "warp16", "warp16u2", "lane", "lane32",
-                             "adaptive"],
-                    help="seglayouts suite: only this kernel form and shape (profiling runs)")
+    ap.add_argument("--seg-form", default=None,
+                    help="seglayouts suite: only these kernel forms and shapes, comma-separated (ldg256, dense256, "
+                         "ldg512, dense512, tma, warp16, warp16u2, lane, lane32, adaptive)")
     ap.add_argument("--soak-seconds", type=float, default=0.5,
                     help="untimed back-to-back load before the timed region (clock sampling window)")
     args = ap.parse_args()

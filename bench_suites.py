@@ -426,6 +426,9 @@ def seglayouts_suite(args):
              "lane32": ((256, 32, 4), sr.F_LANE_SEGMENTS), "adaptive": ((256, 16, 2), sr.F_ADAPTIVE_SEGMENTS)}
     only = getattr(args, "layout", None)
     form = getattr(args, "seg_form", None)
+    chosen = set(form.split(",")) if form else None
+    if chosen and not chosen <= set(forms):
+        raise SystemExit("unknown --seg-form: %s" % ",".join(sorted(chosen - set(forms))))
     for name, off in cases:
         if only and only not in name:
             continue
@@ -435,7 +438,7 @@ def seglayouts_suite(args):
         od = torch.from_numpy(off).cuda()
         out = torch.empty(nseg, dtype=torch.float32, device="cuda")
         for key, (shape, flags) in forms.items():
-            if form and key != form:
+            if chosen and key not in chosen:
                 continue
             cfg = sr.make_config(sr.ATOMIC | flags, block_threads=shape[0], vec_bytes=shape[1], unroll=shape[2],
                                  stages=2 if flags & sr.F_BULK else 0)
@@ -449,7 +452,7 @@ def seglayouts_suite(args):
                    "dense": bool(flags & sr.F_DENSE_SEGMENTS), "bulk": bool(flags & sr.F_BULK),
                    "warp": bool(flags & sr.F_WARP_SEGMENTS), "lane": bool(flags & sr.F_LANE_SEGMENTS),
                    "adaptive": bool(flags & sr.F_ADAPTIVE_SEGMENTS),
-                   "shape": "%d threads x %d B x unroll %d" % shape,
+                   "form": key, "shape": "%d threads x %d B x unroll %d" % shape,
                    "ran": "%d threads x %d B x unroll %d%s" % (r.block_threads, r.vec_bytes, r.unroll,
                                                                ", %d stages" % r.stages if r.stages else ""),
                    "us": round(ms * 1e3, 2),
