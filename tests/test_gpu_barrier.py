@@ -114,3 +114,61 @@ def test_launch_kind_guards(sr):
     with pytest.raises(sr.SRError) as e:   # more cooperative CTAs than can be co-resident
         sr.barrier_bench(sr.LEVEL_KERNEL, reps=2, method=sr.LAUNCH_COOPERATIVE, blocks=sms * 1000)
     assert e.value.status == sr.ERR_LAUNCH
+
+
+# ------------------------------------------------ relations Section V fixes
+def _sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def test_barrier_hierarchy_costs_grow_level_by_level(sr):
+    """Section V / Table II: each level of the hierarchy costs more than the one
+    below it, at the same 128-thread CTA: a coalesced-group sync, a block
+    barrier, a cluster barrier (distributed over SMs) and grid.sync()."""
+    co = sr.barrier_bench(sr.LEVEL_COALESCED, iters=20000, group=32, reps=3)["cycles_per_sync"]
+    bl = sr.barrier_bench(sr.LEVEL_BLOCK, iters=20000, threads=128, reps=3)["cycles_per_sync"]
+    cl = sr.barrier_bench(sr.LEVEL_CLUSTER, iters=20000, cluster=2, threads=128, reps=3)["cycles_per_sync"]
+    gr = sr.barrier_bench(sr.LEVEL_GRID, iters=2000, blocks=_sms(), threads=128, reps=3)["cycles_per_sync"]
+    assert co < bl < cl < gr, (co, bl, cl, gr)
+    assert cl > 5 * bl and gr > 2 * cl, (bl, cl, gr)
+
+
+def test_block_barrier_cost_grows_with_block_size(sr):
+    """Section V-B: __syncthreads() waits for every warp of the block, so its
+    latency grows with the block's warps (one CTA per SM)."""
+    c = {t: sr.barrier_bench(sr.LEVEL_BLOCK, iters=20000, threads=t, reps=3)["cycles_per_sync"]
+         for t in (32, 128, 256, 1024)}
+    assert c[32] < c[128] < c[256] < c[1024], c
+    assert c[1024] > 2.5 * c[32], c
+
+
+def test_ctas_on_different_sms_do_not_interact(sr):
+    """One CTA per SM: the block barrier costs the same on one SM as on every
+    SM (the barrier is local to the SM; Section V-B)."""
+    for threads in (32, 256):
+        one = sr.barrier_bench(sr.LEVEL_BLOCK, iters=20000, threads=threads, blocks=1, reps=3)
+        full = sr.barrier_bench(sr.LEVEL_BLOCK, iters=20000, threads=threads, blocks=_sms(), reps=3)
+        assert full["cycles_per_sync"] == pytest.approx(one["cycles_per_sync"], rel=0.05), threads
+
+
+def test_grid_sync_latency_follows_ctas_per_sm(sr):
+    """Section V-C: grid.sync() latency is governed by the CTAs each SM holds,
+    not by how many SMs take part: one CTA on one SM and one CTA on every SM
+    cost about the same; eight CTAs per SM cost far more."""
+    sms = _sms()
+    r1 = sr.barrier_bench(sr.LEVEL_GRID, iters=2000, blocks=1, threads=32, reps=3)["ns_per_sync"]
+    rs = sr.barrier_bench(sr.LEVEL_GRID, iters=2000, blocks=sms, threads=32, reps=3)["ns_per_sync"]
+    r8 = sr.barrier_bench(sr.LEVEL_GRID, iters=2000, blocks=8 * sms, threads=32, reps=3)["ns_per_sync"]
+    assert rs < 1.25 * r1, (r1, rs)
+    assert r8 > 1.5 * rs, (rs, r8)
+
+
+def test_clock64_and_host_differential_agree(sr):
+    """The two timing methods of Section IX: clock64 counts inside the kernel
+    (slowest warp) and the host-clock differential of Eq. 7 over 10^5 and 10^4
+    syncs, converted with the SM clock, give the same cost per barrier."""
+    for threads in (32, 256, 1024):
+        r = sr.barrier_bench(sr.LEVEL_BLOCK, iters=100000, threads=threads, reps=5)
+        from_ns = r["ns_per_sync"] * r["clock_mhz"] / 1e3
+        assert from_ns == pytest.approx(r["cycles_per_sync"], rel=0.2), (threads, r)
