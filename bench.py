@@ -254,6 +254,8 @@ def main():
                     help="secondary measurement suites (JSON lines); the default run is the headline")
     ap.add_argument("--layout", default=None,
                     help="seglayouts suite: only the layouts whose name contains this text (profiling runs)")
+    ap.add_argument("--shape-cases", default="all", choices=["all", "comp_mid"],
+                    help="shapes suite: every case, or only the compensated 2-64 MiB ones")
     ap.add_argument("--seg-form", default=None,
                     help="seglayouts suite: only these kernel forms and shapes, comma-separated (ldg256, dense256, "
                          "ldg512, dense512, tma, warp16, warp16u2, lane, lane32, adaptive)")

@@ -245,6 +245,11 @@ def shapes_suite(args):
     eb = {sr.F32: 4, sr.I32: 4, sr.BF16: 2, sr.FP8E4M3: 1}
     cases = [(sr.F32, 0, k) for k in (20, 22, 24, 26, 27, 28, 30)] + [(sr.F32, K, k) for k in (26, 27, 28, 30)]
     cases += [(dt, c, k) for dt in (sr.BF16, sr.FP8E4M3) for c in (0, K) for k in (28, 30)]
+    # compensated inputs of 2, 16 and 64 MiB (the two-kernel regime below 64 MiB)
+    comp_mid = [(sr.F32, K, k) for k in (19, 22, 24)] + [(sr.BF16, K, k) for k in (20, 23, 25)]
+    comp_mid += [(sr.FP8E4M3, K, k) for k in (21, 24, 26)]
+    which = getattr(args, "shape_cases", "all")
+    cases = comp_mid if which == "comp_mid" else cases + comp_mid
     for dt, comp, k in cases:
         n = 1 << k
         calls = 40 if k <= 22 else (8 if k <= 26 else 3)

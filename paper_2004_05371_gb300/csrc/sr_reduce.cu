@@ -167,16 +167,20 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
                 // decode sets the pace, keeps two in flight)
                 def_vec = 32;
                 def_unroll = bytes >= (16 << 20) && dtype != SR_FP8E4M3 ? 8 : 2;
-            } else if (dtype != SR_F32 || bytes >= (8 << 20)) {
-                // compensated: 256-bit loads as well, 512 x 2 per thread below
-                // 32 MiB, 1024 x 8 (FP8 x 4) above (warm + cold graph sweeps at
-                // 2-64 MiB: e.g. 64 MiB FP32 8.6 / 17.6 us against 15.5 / 16.4
-                // with 16-byte loads, BF16 11.4 / 18.1 against 18.6 / 19.1;
-                // FP32 below 8 MiB keeps 512 x 16 B x 4, 5 % ahead at 4 MiB)
+            } else {
+                // compensated: 256-bit loads as well; 256 x 2 per thread below
+                // 8 MiB (the work-sized grid then spans more SMs), 1024 x 4 up
+                // to 32 MiB, 1024 x 8 (FP8 x 4) above (warm + cold graph sweeps
+                // at 2, 16 and 64 MiB per dtype: 16-byte loads were 10-45 %
+                // behind warm, e.g. 64 MiB FP32 15.5 us against 8.6)
                 def_vec = 32;
-                const bool big = bytes >= (32 << 20);
-                def_block = big ? 1024 : 512;
-                def_unroll = big ? (dtype == SR_FP8E4M3 ? 4 : 8) : 2;
+                if (bytes < (8 << 20)) {
+                    def_block = 256;
+                    def_unroll = 2;
+                } else {
+                    def_block = 1024;
+                    def_unroll = bytes < (32 << 20) ? 4 : (dtype == SR_FP8E4M3 ? 4 : 8);
+                }
             }
         } else {
             p.stage = SR_LAST_BLOCK;

@@ -39,9 +39,9 @@ def test_plan_auto_regimes(sr):
     assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 4, 512) and not r.variant & sr.F_BULK
     r = sr.plan(1 << 28, sr.F32, sr.make_config(sr.F_KAHAN))
     assert r.variant & sr.F_BULK and r.tile_bytes == 32768 and r.stages == 4
-    # compensated, 1-64 MiB: 256-bit loads (FP32 from 8 MiB), 512 x 2 below 32 MiB, 1024 x 8 (FP8 x 4) above
-    for n, dt, shape in (((1 << 20), sr.F32, (16, 4, 512)), ((1 << 22), sr.F32, (32, 2, 512)),
-                         ((1 << 24), sr.F32, (32, 8, 1024)), ((1 << 21), sr.BF16, (32, 2, 512)),
+    # compensated, 1-64 MiB: 256-bit loads; 256 x 2 below 8 MiB, 1024 x 4 to 32 MiB, 1024 x 8 (FP8 x 4) above
+    for n, dt, shape in (((1 << 19), sr.F32, (32, 2, 256)), ((1 << 22), sr.F32, (32, 4, 1024)),
+                         ((1 << 24), sr.F32, (32, 8, 1024)), ((1 << 21), sr.BF16, (32, 2, 256)),
                          ((1 << 25), sr.BF16, (32, 8, 1024)), ((1 << 26), sr.FP8E4M3, (32, 4, 1024))):
         r = sr.plan(n, dt, sr.make_config(sr.F_KAHAN))
         assert (r.vec_bytes, r.unroll, r.block_threads) == shape, (n, dt, r.as_dict())
