@@ -254,8 +254,9 @@ def main():
                     help="secondary measurement suites (JSON lines); the default run is the headline")
     ap.add_argument("--layout", default=None,
                     help="seglayouts suite: only the layouts whose name contains this text (profiling runs)")
-    ap.add_argument("--shape-cases", default="all", choices=["all", "comp_mid"],
-                    help="shapes suite: every case, or only the compensated 2-64 MiB ones")
+    ap.add_argument("--shape-cases", default="all", choices=["all", "comp_mid", "gaps"],
+                    help="shapes suite: every case, only the compensated 2-64 MiB ones, or only plain BF16 / "
+                         "FP8 / int32 below 512 MiB and int32 above")
     ap.add_argument("--seg-form", default=None,
                     help="seglayouts suite: only these kernel forms and shapes, comma-separated (ldg256, dense256, "
                          "ldg512, dense512, tma, warp16, warp16u2, lane, lane32, adaptive)")

@@ -248,8 +248,11 @@ def shapes_suite(args):
     # compensated inputs of 2, 16 and 64 MiB (the two-kernel regime below 64 MiB)
     comp_mid = [(sr.F32, K, k) for k in (19, 22, 24)] + [(sr.BF16, K, k) for k in (20, 23, 25)]
     comp_mid += [(sr.FP8E4M3, K, k) for k in (21, 24, 26)]
+    # plain BF16, FP8 and int32 below 512 MiB, and int32 above
+    gaps = [(sr.BF16, 0, k) for k in (20, 23, 25, 26, 27)] + [(sr.FP8E4M3, 0, k) for k in (21, 24, 26, 27)]
+    gaps += [(sr.I32, 0, k) for k in (19, 22, 24, 26, 28)]
     which = getattr(args, "shape_cases", "all")
-    cases = comp_mid if which == "comp_mid" else cases + comp_mid
+    cases = {"comp_mid": comp_mid, "gaps": gaps}.get(which, cases + comp_mid + gaps)
     for dt, comp, k in cases:
         n = 1 << k
         calls = 40 if k <= 22 else (8 if k <= 26 else 3)

@@ -164,9 +164,18 @@ int reduce_plan(const void* x, int64_t n, int dtype, const sr_config& c, const D
             if (!p.comp) {
                 // 256-bit loads: inputs of this size are often still in L2,
                 // where wider requests double the throughput (FP8, whose
-                // decode sets the pace, keeps two in flight)
+                // decode sets the pace, keeps two in flight); below 4 MiB
+                // 16 KiB per CTA, so the work-sized grid spans every SM: 256
+                // threads x 32 B x 2, or for BF16 / FP8 (twice the threads to
+                // decode) 512 x 16 B x 2 (2 MiB: 2.6-2.8 us against 3.1-3.4
+                // with 512 x 32 B x 2)
                 def_vec = 32;
                 def_unroll = bytes >= (16 << 20) && dtype != SR_FP8E4M3 ? 8 : 2;
+                if (bytes < (4 << 20)) {
+                    const bool narrow = dtype == SR_BF16 || dtype == SR_FP8E4M3;
+                    def_block = narrow ? 512 : 256;
+                    def_vec = narrow ? 16 : 32;
+                }
             } else {
                 // compensated: 256-bit loads as well; 256 x 2 per thread below
                 // 8 MiB (the work-sized grid then spans more SMs), 1024 x 4 up

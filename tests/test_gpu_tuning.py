@@ -25,6 +25,12 @@ def test_plan_auto_regimes(sr):
         assert (r.variant & sr.CLUSTER_MASK) >> sr.CLUSTER_SHIFT == log2c, n
     r = sr.plan(1 << 27, sr.F32)
     assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 1, 512) and not r.variant & sr.F_BULK
+    # plain, 1-64 MiB: 256-bit loads; below 4 MiB 16 KiB per CTA (BF16 / FP8: 512 x 16 B x 2)
+    for n, dt, shape in (((1 << 19), sr.F32, (32, 2, 256)), ((1 << 20), sr.BF16, (16, 2, 512)),
+                         ((1 << 21), sr.FP8E4M3, (16, 2, 512)), ((1 << 19), sr.I32, (32, 2, 256)),
+                         ((1 << 20), sr.F32, (32, 2, 512)), ((1 << 22), sr.I32, (32, 8, 512))):
+        r = sr.plan(n, dt)
+        assert (r.vec_bytes, r.unroll, r.block_threads) == shape, (n, dt, r.as_dict())
     for n, shape in (((1 << 10), (1, 128, 2)), ((1 << 12), (1, 512, 2)), ((1 << 14), (8, 256, 2)),
                      ((1 << 16), (16, 512, 2)), ((1 << 18), (16, 1024, 4))):
         r = sr.plan(n, sr.F32)
