@@ -11,6 +11,7 @@
 // file but never applied on another.
 #include <unistd.h>
 
+#include <atomic>
 #include <cerrno>
 #include <cmath>
 #include <cstdio>
@@ -129,8 +130,13 @@ bool parse_config(const std::vector<std::string>& f, size_t at, sr_config* c) {
 
 // Writes `text` to `path` through a temporary file in the same directory and
 // a rename, so a reader never sees a partly written file.
+std::atomic<unsigned long long> g_tmp_seq{0};
+
 int write_atomically(const std::string& path, const std::string& text) {
-    const std::string tmp = path + ".tmp." + std::to_string((long long)getpid());
+    // process id and a per-process sequence number: concurrent writers, in
+    // this process or another, never share a temporary file
+    const std::string tmp = path + ".tmp." + std::to_string((long long)getpid()) + "." +
+                            std::to_string(g_tmp_seq.fetch_add(1));
     FILE* fp = std::fopen(tmp.c_str(), "wb");
     if (!fp) return SR_ERR_ARG;
     const bool ok = std::fwrite(text.data(), 1, text.size(), fp) == text.size();

@@ -235,3 +235,19 @@ def test_selector_file_well_formed_reaches_the_device_check(lib, tmp_path):
     assert not h.value
     assert lib.sr_selector_load(str(tmp_path / "missing").encode(), sr.ctypes.byref(h)) == sr.ERR_ARG
     assert lib.sr_selector_load(str(p).encode(), None) == sr.ERR_ARG
+
+
+def test_concurrent_saves_leave_one_whole_file(clean_memo, tmp_path):
+    """Writers racing on one path (threads here; processes alike) each write a
+    temporary file of their own and rename it: the survivor parses whole and
+    no temporary file is left behind."""
+    import concurrent.futures as cf
+    src = tmp_path / "in.txt"
+    src.write_text(TABLE)
+    sr.tune_load(str(src))
+    dst = tmp_path / "shared.txt"
+    with cf.ThreadPoolExecutor(8) as ex:
+        sts = list(ex.map(lambda _: sr.lib().sr_tune_save(str(dst).encode()), range(64)))
+    assert all(st == sr.OK for st in sts)
+    assert _entries(dst.read_text()) == _entries(TABLE)
+    assert sorted(p.name for p in tmp_path.iterdir()) == ["in.txt", "shared.txt"]
