@@ -27,10 +27,16 @@ def test_plan_auto_regimes(sr):
     assert (r.vec_bytes, r.unroll, r.block_threads) == (16, 1, 512) and not r.variant & sr.F_BULK
     # plain, 1-64 MiB: 256-bit loads; below 4 MiB 16 KiB per CTA (BF16 / FP8: 512 x 16 B x 2)
     for n, dt, shape in (((1 << 19), sr.F32, (32, 2, 256)), ((1 << 20), sr.BF16, (16, 2, 512)),
-                         ((1 << 21), sr.FP8E4M3, (16, 2, 512)), ((1 << 19), sr.I32, (32, 2, 256)),
-                         ((1 << 20), sr.F32, (32, 2, 512)), ((1 << 22), sr.I32, (32, 8, 512))):
+                         ((1 << 21), sr.FP8E4M3, (16, 2, 512)),
+                         ((1 << 20), sr.F32, (32, 2, 512))):
         r = sr.plan(n, dt)
         assert (r.vec_bytes, r.unroll, r.block_threads) == shape, (n, dt, r.as_dict())
+    # int32, 1-64 MiB: exact in any order, so the atomic finish from 4 MiB (256 x 32 B x 4, x 8 from 32 MiB)
+    for n, stage, shape in (((1 << 19), sr.TWO_KERNEL, (16, 4, 256)), ((1 << 20), sr.ATOMIC, (32, 4, 256)),
+                            ((1 << 22), sr.ATOMIC, (32, 4, 256)), ((1 << 24), sr.ATOMIC, (32, 8, 256))):
+        r = sr.plan(n, sr.I32)
+        assert r.variant & sr.STAGE_MASK == stage and (r.vec_bytes, r.unroll, r.block_threads) == shape, \
+            (n, r.as_dict())
     for n, shape in (((1 << 10), (1, 128, 2)), ((1 << 12), (1, 512, 2)), ((1 << 14), (8, 256, 2)),
                      ((1 << 16), (16, 512, 2)), ((1 << 18), (16, 1024, 4))):
         r = sr.plan(n, sr.F32)
