@@ -286,8 +286,10 @@ int sr_plan(int64_t n, int dtype, const sr_config* cfg, sr_config* resolved);
  * The concatenated range is split evenly over the warps of one persistent
  * grid whatever the segment lengths; segments crossing a warp boundary are
  * finished by the configured grid stage: SR_TWO_KERNEL, SR_GRID_SYNC,
- * SR_LAST_BLOCK (default; per-segment tickets) or SR_ATOMIC (out zeroed
- * first; FP order not deterministic).  All other forms are deterministic.
+ * SR_LAST_BLOCK (per-segment tickets; the SR_AUTO default for floating-point
+ * inputs) or SR_ATOMIC (out zeroed first; FP order not deterministic; the
+ * SR_AUTO default for SR_I32, whose int64 sums are exact in any order).  All
+ * other forms are deterministic.
  * Load path: rows of 16/32-byte vectors loaded into registers (LDG), or with
  * SR_F_BULK each warp streams its piece through its own ring of `stages`
  * (2..8, default 2) chunks of `unroll` rows (2, 4 or 8; default 4) in shared
